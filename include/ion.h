@@ -1,0 +1,304 @@
+/*
+ * ion.h -- C ABI of the GB300 InfOli network simulator (libion.so).
+ *
+ * The library advances networks of three-compartment inferior-olive cells coupled by
+ * dendritic gap junctions, one synchronous explicit-Euler step at a time, on one GPU.
+ * Paper: Smaragdos et al., "BrainFrame: a node-level heterogeneous accelerator
+ * platform for neuron simulations" (arXiv 1612.01501):
+ *   - Sec. 2.2 "The InfOli Workload": a new cell state depends only on the cell's
+ *     previous state, the previous dendritic voltages of its gap-junction partners and
+ *     the evoked input; compartments and gap junctions are updated concurrently with a
+ *     fixed 50 us step.  Table "reqs": 19 state words, 20 conductances, 1 evoked input
+ *     and 1 connectivity word per connection per cell.
+ *   - Algorithm 1 (RGJ): Ic_i += w_ij (0.8 e^{-dV^2/100} + 0.2) dV, dV = V_dend,i - V_dend,j.
+ *   - Sec. 2.3: connectivity is a user-programmed weight matrix; here either one
+ *     uniform weight for every pair (dense all-to-all) or a CSR matrix.
+ *   - Sec. 2.4.3: states and evoked inputs are copied to the device once before the
+ *     run; no host data is needed while it runs.
+ *
+ * Conventions for every entry point:
+ *   - Each call returns an ion_status and never aborts or exits the process.
+ *   - Host buffers passed in are copied before the call returns; the caller keeps
+ *     ownership.  Buffers marked ION_DEVICE are read in place (borrowed) and must stay
+ *     valid for as long as the documentation of the argument says.
+ *   - Work is enqueued on the CUDA stream given in ion_params.cuda_stream (NULL: a
+ *     non-blocking stream the handle creates and owns).  ion_step is asynchronous; errors the device detects
+ *     (a non-finite state, a barrier that timed out) are sticky and are returned by
+ *     the next ion_sync / ion_read_* call.
+ *   - A handle is used by one host thread at a time.
+ *   - Units: mV, ms, mS/cm^2, uF/cm^2, uA/cm^2; [Ca] in the model's units.
+ *   - State is structure-of-arrays: field f of cell i is element f * n_cells + i of a
+ *     full-state buffer, fields in the order of enum ion_field.
+ */
+#ifndef ION_H
+#define ION_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ION_NFIELDS 19 /* Table "reqs": 19 state words per cell */
+#define ION_NPARAMS 25 /* model constants, order of enum ion_param */
+#define ION_NGATES 12  /* gating variables with a rate function */
+
+typedef enum {
+    ION_OK = 0,
+    ION_ERR_INVALID_ARG = 1, /* a NULL pointer, a size out of range, an unknown enum   */
+    ION_ERR_BAD_CSR = 2,     /* CSR not monotone, index out of range, self loop,
+                                unsorted row, or not symmetric                          */
+    ION_ERR_OOM = 3,         /* device or host allocation failed                       */
+    ION_ERR_CUDA = 4,        /* a CUDA runtime call failed (see ion_last_error)        */
+    ION_ERR_NONFINITE = 5,   /* the device saw a NaN or Inf in a voltage or [Ca]       */
+    ION_ERR_TIMEOUT = 6,     /* a bounded device wait (grid barrier) gave up           */
+    ION_ERR_UNSUPPORTED = 7  /* valid request this build does not handle               */
+} ion_status;
+
+/* State fields (Table "reqs": 19 words).  m_s, m_a, I_CaH and I_c hold the values used
+ * during the last step (they are outputs, never read back by the update); g_CaL is a
+ * per-cell constant. */
+enum ion_field {
+    ION_V_DEND = 0, ION_V_SOMA, ION_V_AXON, ION_CA,
+    ION_R, ION_S, ION_Q,                         /* dendrite gates              */
+    ION_K, ION_L, ION_M_S, ION_H_S, ION_N_S, ION_X_S, /* soma gates             */
+    ION_M_A, ION_H_A, ION_X_A,                   /* axon gates                  */
+    ION_G_CAL, ION_I_CAH, ION_I_C,
+    ION_FIELD_ALL = -1                           /* all 19 fields, SoA order    */
+};
+
+/* Model constants (the "20 conductances" of Table "reqs" are entries 0..19). */
+enum ion_param {
+    ION_P_GINT = 0, ION_P_P1, ION_P_P2,
+    ION_P_GCAH, ION_P_GKCA, ION_P_GH, ION_P_GLD,
+    ION_P_GCAL, ION_P_GNAS, ION_P_GKDRS, ION_P_GKS, ION_P_GLS,
+    ION_P_GNAA, ION_P_GKA, ION_P_GLA,
+    ION_P_VNA, ION_P_VK, ION_P_VCA, ION_P_VH, ION_P_VL,
+    ION_P_CM, ION_P_CA_IN, ION_P_CA_OUT, ION_P_V0, ION_P_CA0
+};
+
+enum ion_net_kind {
+    ION_DENSE_UNIFORM = 0, /* all-to-all, one weight g_c for every pair (RGJ, C = 100 %) */
+    ION_CSR = 1,           /* CSR weight matrix (RGJ at any density)                     */
+    ION_NO_GJ = 2          /* independent cells (NGJ use case, Sec. 2.3.3)               */
+};
+enum ion_mem { ION_HOST = 0, ION_DEVICE = 1 };
+
+enum ion_flag {
+    ION_FLAG_KAHAN = 1u << 0,      /* compensated dense gap-junction sums (default on)     */
+    ION_FLAG_PERSISTENT = 1u << 1, /* keep state on chip across steps where it fits        */
+    ION_FLAG_SURROGATE = 1u << 2,  /* MLP surrogate for the channel rate functions         */
+    ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
+    ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
+    ION_FLAG_SPLIT = 1u << 5       /* separate gap-junction and cell-update kernels         */
+};
+
+typedef struct {
+    int32_t n_cells; /* >= 1 */
+    int32_t kind;    /* enum ion_net_kind */
+} ion_net;
+
+/* Connectivity.  Dense: g_c is the weight of every pair.  CSR: row_ptr[n+1] (int32,
+ * row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz), col_idx[nnz] in [0, n), strictly
+ * ascending within a row, no self loops, pattern symmetric; weight[nnz] (may be NULL:
+ * every weight is g_c).  mem says where the three arrays live; ION_DEVICE arrays are
+ * borrowed and must outlive the handle.  The symmetry check is done for host arrays
+ * only (device arrays are trusted). */
+typedef struct {
+    float g_c;
+    const int32_t *row_ptr;
+    const int32_t *col_idx;
+    const float *weight;
+    int64_t nnz;
+    int32_t mem;
+} ion_conn;
+
+typedef struct {
+    double v[ION_NPARAMS];
+} ion_model;
+
+typedef struct {
+    double dt_ms;               /* 0 means 0.05 (the paper's 50 us step)                  */
+    const ion_model *model;     /* NULL means ion_model_default()                         */
+    uint32_t flags;             /* enum ion_flag                                          */
+    const void *surrogate;      /* ion_surrogate_weights* when ION_FLAG_SURROGATE          */
+    int32_t check_every;        /* steps between non-finite scans (0 = 64)                */
+    int32_t graph_steps;        /* steps captured per CUDA graph (0 = 50)                 */
+    uint64_t barrier_timeout_ns;/* bound on a persistent kernel's grid barrier (0 = 2 s)  */
+    void *cuda_stream;          /* cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream;
+                                   NULL: the handle creates and owns a non-blocking stream  */
+    const void *tune;           /* ion_tune* launch shape override, NULL = built-in choice */
+} ion_params;
+
+/* Evoked input (Sec. 2.2: one evoked-input word per cell per step).
+ *   ION_INPUT_NONE   -- no evoked current;
+ *   ION_INPUT_PULSES -- I_app(t, i) = sum of amp[p] over pulses p with cell[p] == i and
+ *                       t_begin[p] <= t < t_end[p] (t = absolute step index);
+ *   ION_INPUT_DENSE  -- I_app(t, i) = dense[(t - t_first) * n_cells + i] for the
+ *                       n_steps of one ion_step call (t_first = its first step). */
+enum ion_input_kind { ION_INPUT_NONE = 0, ION_INPUT_PULSES = 1, ION_INPUT_DENSE = 2 };
+typedef struct {
+    int32_t kind;
+    int32_t mem;           /* where dense / pulse arrays live                        */
+    const float *dense;    /* [n_steps x n_cells], row-major                          */
+    int32_t n_pulses;
+    const int32_t *pulse_cell;
+    const int64_t *pulse_begin;
+    const int64_t *pulse_end;
+    const float *pulse_amp;
+} ion_input;
+
+/* Launch-shape override (filled by the autotuner, or by hand). 0 = choose. */
+typedef struct {
+    int32_t dense_rows_per_warp; /* 1, 2, 4, 6 or 8                                 */
+    int32_t dense_warps;         /* warps per CTA, 1..16                            */
+    int32_t csr_lanes_per_row;   /* 1, 2, 4, 8, 16 or 32                            */
+    int32_t csr_rows_per_cta;    /* 32..1024, multiple of 32                        */
+    int32_t batch_tile_pairs;    /* work per batched tile, in pair evaluations      */
+} ion_tune;
+
+typedef struct ion_sim ion_sim;
+
+/* ---- model -------------------------------------------------------------------- */
+
+/* The library's constants table (its own copy; the oracle keeps another). */
+void ion_model_default(ion_model *out);
+
+/* Every gate's steady state and time constant at voltage V and calcium ca, FP32, as
+ * the device computes them (gate order: r s q k l m_s h_s n_s x_s m_a h_a x_a; tau of
+ * the instantaneous m_s, m_a is 0).  xinf and tau are host arrays of 12 floats each. */
+ion_status ion_rates(float V, float ca, float *xinf, float *tau);
+
+/* Default initial state of n cells into host buffer out[19 * n] (FP32, SoA): every
+ * compartment at V_0, each gate at its steady state there, [Ca] at [Ca]_0. */
+ion_status ion_default_state(const ion_model *model, int32_t n, float *out);
+
+/* ---- simulation handle -------------------------------------------------------- */
+
+/* Validate, copy to the device and prepare launches of one network.
+ * init_state: host FP32 buffer of 19 * n_cells values (SoA) or NULL for the default.
+ * On success *out owns device memory until ion_destroy. */
+ion_status ion_create(const ion_net *net, const ion_conn *conn, const ion_params *params,
+                      const float *init_state, ion_sim **out);
+
+/* Several independent networks advanced together (one launch per step covers all).
+ * Cells are numbered consecutively across networks (network b's cell i is global cell
+ * offset_b + i); state buffers and pulse cells use the global numbering. */
+ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, const ion_conn *conns,
+                            const ion_params *params, const float *init_state,
+                            ion_sim **out);
+
+/* Install the evoked input used by later ion_step calls that pass NULL.  Pulse arrays
+ * are copied; a DENSE input cannot be installed. */
+ion_status ion_set_input(ion_sim *sim, const ion_input *input);
+
+/* Advance n_steps >= 0 steps on the handle's stream (asynchronous).  input NULL uses
+ * the installed input; a DENSE input must hold n_steps x n_cells values and, if it is
+ * ION_DEVICE, stay valid until the stream reaches the end of this call's work. */
+ion_status ion_step(ion_sim *sim, int64_t n_steps, const ion_input *input);
+
+/* Wait for the handle's stream, then report any sticky device error. */
+ion_status ion_sync(ion_sim *sim);
+
+/* Copy state to host memory `out` (count floats: n_cells for one field, 19 * n_cells
+ * for ION_FIELD_ALL).  Synchronises; returns a sticky device error if there is one
+ * (the copy is still made). */
+ion_status ion_read_state(ion_sim *sim, int32_t field, float *out, int64_t count);
+
+/* Overwrite state from host memory `in` (same sizes as ion_read_state).  Ordered on
+ * the handle's stream after earlier steps. */
+ion_status ion_write_state(ion_sim *sim, int32_t field, const float *in, int64_t count);
+
+/* Device pointer of one field of the current state (valid until the next ion_step). */
+ion_status ion_state_device_ptr(ion_sim *sim, int32_t field, float **out);
+
+/* Record V_axon of every cell every `stride` steps into a device ring of `capacity`
+ * samples (0 disables); ion_read_trace copies the samples recorded since the last read
+ * (oldest first) to host memory: out[s * n_cells + i]. */
+ion_status ion_set_trace(ion_sim *sim, int32_t stride, int32_t capacity);
+ion_status ion_read_trace(ion_sim *sim, float *out, int64_t max_samples, int64_t *n_written);
+
+/* Steps taken so far (the absolute index of the next step). */
+int64_t ion_step_count(const ion_sim *sim);
+
+/* Set the absolute index of the next step (checkpoint resume: write the saved state,
+ * then set the saved step count so evoked-input pulses line up).  Synchronises. */
+ion_status ion_set_step_count(ion_sim *sim, int64_t t);
+
+/* Number of kernel launches the handle issued (graph nodes counted once per replay). */
+int64_t ion_launch_count(const ion_sim *sim);
+
+/* Human-readable description of the last error on this handle (NULL: the last error of
+ * a call that had no handle yet, e.g. a failed ion_create). */
+const char *ion_last_error(const ion_sim *sim);
+
+void ion_destroy(ion_sim *sim);
+
+/* ---- single-launch primitives (one step of one stage; device pointers) ------------ */
+
+/* Ic[i] = g_c * sum_j (0.8 e^{-(V_i-V_j)^2/100} + 0.2)(V_i - V_j) for a dense uniform
+ * network (Algorithm 1 with C = 100 %).  vdend, ic: device arrays of n floats.
+ * kahan != 0 compensates the j sums. */
+ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, float *ic, int32_t kahan,
+                        void *cuda_stream);
+
+/* Ic[i] = sum_{e in row i} w[e] (0.8 e^{-dV^2/100} + 0.2) dV, dV = V_i - V_{col[e]}
+ * (Algorithm 1 over a CSR matrix).  All arrays on the device; w NULL means every
+ * weight is g_c. */
+ion_status ion_gj_csr(const float *vdend, int32_t n, const int32_t *row_ptr,
+                      const int32_t *col_idx, const float *w, float g_c, float *ic,
+                      void *cuda_stream);
+
+/* One explicit-Euler cell update of n cells, in place on the device SoA buffer
+ * state[19 * n] (V_dend included), with gap current ic[n] (NULL: none) and evoked
+ * current iapp[n] (NULL: none).  model NULL = default. */
+ion_status ion_cell_update(float *state, int32_t n, const float *ic, const float *iapp,
+                           const ion_model *model, double dt_ms, void *cuda_stream);
+
+/* ---- measurement ------------------------------------------------------------------ */
+
+/* Throughput probe of one execution unit at the current clock: what = 0 measures SFU
+ * ex2.approx results per second, what = 1 FP32 FMAs per second, over the whole GPU
+ * (8 independent chains per thread, 8 CTAs of 256 threads per SM, `iters` rounds).
+ * These are the measured denominators of the dense gap-junction kernel's roofline.
+ * Synchronises the stream.  Not part of the paper's method. */
+ion_status ion_probe_peak(int32_t what, int32_t iters, void *cuda_stream, double *rate_out);
+
+/* ---- learned surrogate of the rate functions ------------------------------------ */
+
+/* MLP 2 -> 64 -> 64 -> 24 (x_inf and log tau of each of the 12 gates) with tanh hidden
+ * units, used in place of the exact rate functions when ION_FLAG_SURROGATE is set.
+ * Weights row-major [out][in]; FP32 master copy. */
+#define ION_MLP_IN 2
+#define ION_MLP_HID 64
+#define ION_MLP_OUT 24
+typedef struct {
+    float w1[ION_MLP_HID * ION_MLP_IN], b1[ION_MLP_HID];
+    float w2[ION_MLP_HID * ION_MLP_HID], b2[ION_MLP_HID];
+    float w3[ION_MLP_OUT * ION_MLP_HID], b3[ION_MLP_OUT];
+    float in_shift[ION_MLP_IN], in_scale[ION_MLP_IN];   /* x' = (x - shift) * scale */
+    float out_shift[ION_MLP_OUT], out_scale[ION_MLP_OUT]; /* y = y' * scale + shift   */
+} ion_surrogate_weights;
+
+typedef struct {
+    int64_t n_samples;   /* training set size (e.g. 1e6)                            */
+    int32_t epochs;
+    int32_t batch;       /* minibatch size, multiple of 128                         */
+    float lr;            /* Adam step size                                          */
+    uint64_t seed;
+    float v_lo, v_hi;    /* V range, mV                                             */
+    float ca_lo, ca_hi;  /* [Ca] range (log-uniform)                                */
+    void *cuda_stream;
+} ion_train_cfg;
+
+/* Train the surrogate on the GPU from samples of the exact FP32 rate functions.
+ * weights_out: host struct, filled on success; final_loss (nullable) gets the mean
+ * squared error of the last epoch. */
+ion_status ion_surrogate_train(const ion_train_cfg *cfg, ion_surrogate_weights *weights_out,
+                               float *final_loss);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ION_H */

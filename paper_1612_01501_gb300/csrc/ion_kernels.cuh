@@ -1,0 +1,99 @@
+// ion_kernels.cuh -- launch arguments and launchers shared by the library's .cu files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "ion_model.cuh"
+
+namespace ion {
+
+// Dense tiles of V_dend are staged TJ floats at a time; every V_dend buffer is padded
+// to a multiple of PAD_J floats with a sentinel voltage far from any physiological
+// value, so padded pairs contribute exactly 0 to the exponential sum.
+constexpr int TJ = 8192;
+constexpr int PAD_J = 256;
+constexpr float PAD_VOLT = 1.0e7f;
+
+// Scale s with (s dV)^2 = dV^2 log2(e) / 100, so e^{-dV^2/100} = 2^{-(s dV)^2}.
+constexpr float GJ_SCALE = 0.12011224087864498f;   // sqrt(log2(e) / 100)
+
+struct StepCommon {
+    StateView S;          // 20 * stride floats: fields 0..18 and the second V_dend slot
+    int32_t n;            // cells
+    int32_t n_pad;        // V_dend length incl. sentinel padding (multiple of PAD_J)
+    const int64_t *t_dev; // absolute index of the first step of the current replay (NULL: t = 0)
+    int32_t k_off;        // this launch's step offset from *t_dev
+    int32_t vd_fixed;     // 1: V_dend is updated in place in slot 0 (single-cell-launch primitives)
+    PulseTable pulses;
+    const float *iapp;    // dense evoked input of this step (n floats) or NULL
+    uint32_t *status;     // sticky status word
+    float *trace;         // V_axon ring [cap][n] or NULL
+    int32_t trace_stride, trace_cap;
+    ModelF P;
+};
+
+// V_dend slot holding step t: slot 0 is field F_VDEND, slot 1 is field 19.
+__device__ __forceinline__ float *vd_slot(const StateView &S, int64_t t) {
+    return S.base + ((t & 1) ? 19 : 0) * S.stride;
+}
+__device__ __forceinline__ int64_t step_index(const StepCommon &c) {
+    return c.t_dev != nullptr ? *c.t_dev + c.k_off : (int64_t)c.k_off;
+}
+__device__ __forceinline__ float *vd_cur(const StepCommon &c, int64_t t) {
+    return c.vd_fixed ? c.S.base : vd_slot(c.S, t);
+}
+__device__ __forceinline__ float *vd_next(const StepCommon &c, int64_t t) {
+    return c.vd_fixed ? c.S.base : vd_slot(c.S, t + 1);
+}
+
+// Write the step result of cell i (and its trace sample, status bit).
+__device__ __forceinline__ void finish_cell(const StepCommon &a, int64_t t, float *vd_next, int64_t i,
+                                            const CellNext &o) {
+    store_cell(a.S, vd_next, i, o);
+    if (!cell_finite(o)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
+    if (a.trace != nullptr && ((t + 1) % a.trace_stride) == 0) {
+        const int64_t sample = (t + 1) / a.trace_stride - 1;
+        a.trace[(sample % a.trace_cap) * (int64_t)a.n + i] = o.va;
+    }
+}
+
+struct DenseArgs {
+    StepCommon c;
+    float g;              // uniform pair weight
+    int32_t fuse;         // 1: cell update in the same launch; 0: write Ic only
+    int32_t kahan;
+    float *ic_out;        // when !fuse: Ic[n]
+    const float *vd_in;   // when !fuse: V_dend[n_pad] (sentinel padded)
+};
+struct CsrArgs {
+    StepCommon c;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const float *w;       // NULL: every weight is g
+    float g;
+    int32_t fuse;
+    float *ic_out;
+    const float *vd_in;
+};
+struct CellArgs {
+    StepCommon c;
+    const float *ic;      // NULL: no gap current
+};
+
+// launchers (return the CUDA launch status)
+cudaError_t launch_dense_step(const DenseArgs &a, int rows_per_warp, int warps, cudaStream_t st);
+cudaError_t launch_csr_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, cudaStream_t st);
+cudaError_t launch_cell_step(const CellArgs &a, cudaStream_t st);
+cudaError_t launch_advance(int64_t *t_dev, int64_t k, cudaStream_t st);
+cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);
+cudaError_t launch_rates(float V, float ca, float *xinf_tau /*24 floats, device*/, cudaStream_t st);
+cudaError_t launch_default_state(const ModelF &P, float V0, float ca0, float gcal, int32_t n, int64_t stride,
+                                 float *state, cudaStream_t st);
+cudaError_t prepare_dense_step(int rows_per_warp, int warps, int n_pad);
+int dense_max_rows_per_warp();
+
+// shared-memory size of a dense launch
+size_t dense_smem_bytes(int n_pad, int rows_per_warp, int warps);
+
+}  // namespace ion

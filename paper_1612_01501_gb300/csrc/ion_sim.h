@@ -1,0 +1,78 @@
+// ion_sim.h -- the handle behind the opaque `ion_sim` of include/ion.h (library-internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "ion.h"
+#include "ion_kernels.cuh"
+
+struct ion_sim {
+    // network
+    int32_t n = 0, kind = 0, n_pad = 0;
+    int64_t stride = 0;
+    float g = 0.0f;                 // dense pair weight / CSR default weight
+    int64_t nnz = 0;
+    int32_t *d_rowptr = nullptr, *d_col = nullptr;
+    float *d_w = nullptr;
+    bool own_csr = false;
+    // state and bookkeeping
+    float *d_state = nullptr;       // 20 * stride floats
+    float *d_ic = nullptr;          // gap currents (split mode)
+    int64_t *d_t = nullptr;         // device step counter
+    uint32_t *d_status = nullptr;   // sticky status bits
+    uint32_t sticky = 0;            // status bits seen by the host
+    int64_t t = 0;                  // host step counter (steps enqueued)
+    int64_t launches = 0;           // kernel launches issued (graph nodes counted per replay)
+    // evoked input
+    int32_t *d_poff = nullptr;
+    int64_t *d_pbeg = nullptr, *d_pend = nullptr;
+    float *d_pamp = nullptr;
+    int32_t n_pulses = 0;
+    float *d_iapp = nullptr;
+    int64_t iapp_cap = 0;
+    // trace
+    float *d_trace = nullptr;
+    int32_t trace_stride = 0, trace_cap = 0;
+    int64_t trace_read = 0;
+    // model and launch configuration
+    ion_model model{};
+    ion::ModelF P{};
+    double dt = 0.05;
+    cudaStream_t st = nullptr;
+    cudaStream_t own_stream = nullptr;   // created when the caller passed no stream
+    uint32_t flags = 0;
+    int32_t graph_steps = 50, check_every = 64;
+    uint64_t barrier_timeout_ns = 0;
+    int device = 0, sms = 1;
+    int dense_R = 1, dense_W = 4, csr_SW = 8, csr_rows = 256;
+    cudaGraphExec_t gexec = nullptr;
+    int64_t graph_launches = 0;
+    bool no_graph = false;
+    std::string err;
+
+    // extension points (persistent, batched and surrogate variants)
+    cudaError_t (*step_override)(ion_sim *, int k_off, const float *iapp) = nullptr;
+    ion_status (*run_override)(ion_sim *, int64_t n_steps, const float *iapp) = nullptr;
+    ion_status (*prepare_hook)(ion_sim *) = nullptr;
+    ion_status (*state_sync_hook)(ion_sim *) = nullptr;
+    ion_status (*state_load_hook)(ion_sim *) = nullptr;
+    void (*extra_free)(ion_sim *) = [](ion_sim *) {};
+    void *ext = nullptr;            // extension state
+    int64_t lps = 1;                // kernel launches per step
+
+    int64_t launches_per_step() const { return lps; }
+};
+
+// shared helpers (ion_api.cu)
+ion_status ion_fail(ion_sim *s, ion_status code, const char *fmt, ...);
+ion::ModelF ion_model_to_f32(const ion_model &m, double dt);
+ion::StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp);
+float *ion_field_ptr(ion_sim *s, int32_t field);
+ion_status ion_validate_csr(int32_t n, const ion_conn *c);
+void ion_choose_dense_shape(int n, int sms, int *R, int *W);
+void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
+void ion_sim_free_device(ion_sim *s);
+// per-flag setup of the extensions (ion_ext.cu)
+ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p);

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library builds and loads, exports every entry point
+include/ion.h declares, its constants table equals the oracle's, and host-side argument
+validation (run before any device call) rejects malformed input with the right code."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1612_01501_gb300 import build as B
+from paper_1612_01501_gb300 import inputs
+from paper_1612_01501_gb300 import ion
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    B.build()
+    return ion.lib()
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "ion.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ion_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(L):
+    syms = declared_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(L, s), s
+    assert set(syms) == set(ion._SIGS), "binding and header disagree"
+
+
+def test_model_table_matches_oracle(L, O):
+    a = ion.ion_model_default()
+    b = O.model_default()
+    np.testing.assert_array_equal(a, b)
+    assert ion.FIELDS == O.FIELDS and ion.GATES == O.GATES
+
+
+def _create_err(**kw):
+    with pytest.raises(ion.IonError) as ei:
+        ion.ion_create(**kw)
+    return ei.value.status
+
+
+def test_invalid_arguments_rejected(L):
+    assert _create_err(n=0, kind=ion.DENSE_UNIFORM, g=0.1) == ion.ERR_INVALID_ARG
+    assert _create_err(n=10, kind=7, g=0.1) == ion.ERR_INVALID_ARG
+    assert _create_err(n=10, kind=ion.DENSE_UNIFORM, g=float("nan")) == ion.ERR_INVALID_ARG
+    assert _create_err(n=10, kind=ion.DENSE_UNIFORM, g=0.1, dt_ms=5.0) == ion.ERR_INVALID_ARG
+    bad = ion.ion_model_default()
+    bad[1] = 1.5    # p1 outside (0, 1)
+    assert _create_err(n=10, kind=ion.DENSE_UNIFORM, g=0.1, model=bad) == ion.ERR_INVALID_ARG
+
+
+def test_malformed_csr_rejected(L):
+    n = 50
+    rp, col = inputs.random_symmetric_csr(n, 6, 1)
+    # out of range index
+    c2 = col.copy()
+    c2[3] = n
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp, col=c2) == ion.ERR_BAD_CSR
+    # self loop
+    c2 = col.copy()
+    c2[rp[4]] = 4
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp, col=c2) == ion.ERR_BAD_CSR
+    # unsorted row
+    c2 = col.copy()
+    r = int(np.argmax(np.diff(rp) >= 2))
+    c2[rp[r]], c2[rp[r] + 1] = c2[rp[r] + 1], c2[rp[r]]
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp, col=c2) == ion.ERR_BAD_CSR
+    # asymmetric: drop one direction of an edge by retargeting it within its row's range
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    keep = ~((rows == 0) & (np.arange(len(col)) == rp[0]))
+    rp2 = np.zeros(n + 1, np.int32)
+    np.cumsum(np.bincount(rows[keep], minlength=n), out=rp2[1:])
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp2, col=col[keep]) == ion.ERR_BAD_CSR
+    # decreasing row_ptr / wrong nnz
+    rp3 = rp.copy()
+    rp3[5] = rp3[6] + 1
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp3, col=col) == ion.ERR_BAD_CSR
+    rp4 = rp.copy()
+    rp4[-1] -= 1
+    assert _create_err(n=n, kind=ion.CSR, row_ptr=rp4, col=col[:-1].copy()) in (ion.ERR_BAD_CSR,)

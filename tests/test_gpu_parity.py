@@ -1,0 +1,288 @@
+"""GPU path vs the FP64 oracle on identical seeded inputs (every test needs a GB300).
+
+Bars (spec tolerances): one step from an identical FP32 state has relative error
+<= 1e-5 (floors: 1 mV, 1e-3 for gates); voltages stay within 0.1 mV of the oracle over the
+first 100 ms; spike times agree within one step over 1 s.  Gap-current primitives are held
+to 2e-6 of sum_j |dV_ij| (the scale of the FP32 rounding of the scaled voltages).
+"""
+import numpy as np
+import pytest
+
+from paper_1612_01501_gb300 import inputs
+from paper_1612_01501_gb300 import ion
+
+from helpers import STEP_RTOL, TRAJ_MV, initial_state, step_rel_err, sum_abs_dv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01501_gb300 import build
+    build.build()
+    return torch
+
+
+def _threads(O):
+    return max(1, O.max_threads())
+
+
+# ------------------------------------------------------------------ model pieces
+
+def test_rates_match_oracle(torch_cuda, O):
+    worst_x = worst_t = 0.0
+    for ca in (0.5, 3.7, 20.0, 800.0):
+        for V in np.arange(-100.0, 60.0, 0.37):
+            V32 = float(np.float32(V))
+            xg, tg = ion.ion_rates(V32, ca)
+            xo, to = O.rates(V32, float(np.float32(ca)))
+            worst_x = max(worst_x, np.max(np.abs(xg - xo) / np.maximum(np.abs(xo), 1e-3)))
+            m = to > 0
+            worst_t = max(worst_t, np.max(np.abs(tg[m] - to[m]) / to[m]))
+    assert worst_x < 2e-6, worst_x
+    assert worst_t < 2e-6, worst_t
+
+
+def test_default_state_matches_oracle(torch_cuda, O):
+    g = ion.ion_default_state(5)
+    o = O.default_state(5)
+    assert step_rel_err(g, o).max() < 2e-6
+
+
+# ------------------------------------------------------------------ gap-junction primitives
+
+@pytest.mark.parametrize("n", [1, 2, 63, 1000, 8192, 16461])
+@pytest.mark.parametrize("kahan", [True, False])
+def test_gj_dense_primitive(torch_cuda, O, n, kahan):
+    torch = torch_cuda
+    vd = (-60.0 + inputs.vdend_jitter(n, 100 + n, 20.0)).astype(np.float32)
+    g = inputs.junction_weight(0.04, max(n, 1))
+    ic = torch.empty(n, dtype=torch.float32, device="cuda")
+    ion.ion_gj_dense(torch.from_numpy(vd).cuda(), g, ic, kahan=kahan)
+    torch.cuda.synchronize()
+    ref = O.gj_dense(vd.astype(np.float64), float(np.float32(g)), threads=_threads(O))
+    tol = 2e-6 * g * sum_abs_dv(vd) + 1e-30
+    err = np.abs(ic.cpu().numpy() - ref)
+    assert np.all(err <= tol), (err / tol).max()
+
+
+@pytest.mark.parametrize("n,k", [(5000, 10), (5000, 100), (3001, 1000), (100, 0)])
+def test_gj_csr_primitive(torch_cuda, O, n, k):
+    torch = torch_cuda
+    rp, col = inputs.random_symmetric_csr(n, k, 7)
+    w = inputs.uniform(inputs.stream_seed(k, "w"), len(col), 0.001, 0.05).astype(np.float32)
+    vd = (-60.0 + inputs.vdend_jitter(n, 9, 20.0)).astype(np.float32)
+    ic = torch.empty(n, dtype=torch.float32, device="cuda")
+    T = lambda a: torch.from_numpy(a).cuda()
+    ion.ion_gj_csr(T(vd), T(rp), T(col) if len(col) else torch.zeros(1, dtype=torch.int32, device="cuda"),
+                   T(w) if len(w) else None, 0.0, ic)
+    torch.cuda.synchronize()
+    ref = O.gj_csr(rp, col, w.astype(np.float64), vd.astype(np.float64))
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    scale = np.bincount(rows, weights=w * np.abs(vd[rows] - vd[col]), minlength=n) if len(col) else np.zeros(n)
+    err = np.abs(ic.cpu().numpy() - ref)
+    assert np.all(err <= 2e-6 * scale + 1e-30)
+
+
+# ------------------------------------------------------------------ one step from an identical state
+
+def _one_step_case(O, name, n, kind, g=0.0, rp=None, col=None, w=None, warm=50, **kw):
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 31))
+    S0 = initial_state(O, cfg)
+    k_or = {O.DENSE: O.DENSE, O.CSR: O.CSR, O.NOGJ: O.NOGJ}[kind]
+    wd = None if w is None else w.astype(np.float64)
+    # warm the state up with the oracle so every variable is off its steady state
+    Sw, _ = O.run(S0.astype(np.float64), warm, kind=k_or, g=g, row_ptr=rp, col=col, w=wd, threads=_threads(O))
+    Sw32 = Sw.astype(np.float32)
+    iapp = inputs.uniform(inputs.stream_seed(n, "iapp"), n, 0.0, 4.0).astype(np.float32)
+    ref, _ = O.run(Sw32.astype(np.float64), 1, kind=k_or, g=g, row_ptr=rp, col=col, w=wd, t0=0,
+                   iapp_dense=iapp[None, :], threads=_threads(O))
+    ikind = {O.DENSE: ion.DENSE_UNIFORM, O.CSR: ion.CSR, O.NOGJ: ion.NO_GJ}[kind]
+    with ion.Simulation(n, ikind, g=g, row_ptr=rp, col=col, w=w, init_state=Sw32, **kw) as sim:
+        sim.step(1, dense=iapp[None, :])
+        got = sim.state()
+    err = step_rel_err(got, ref)
+    return err
+
+
+@pytest.mark.parametrize("n", [1, 64, 300, 8192])
+@pytest.mark.parametrize("flags", [ion.FLAG_KAHAN, ion.FLAG_KAHAN | ion.FLAG_SPLIT])
+def test_one_step_dense(torch_cuda, O, n, flags):
+    g = inputs.junction_weight(0.04, n)
+    err = _one_step_case(O, "dense", n, O.DENSE, g=float(np.float32(g)), flags=flags)
+    assert err.max() <= STEP_RTOL, (err.max(axis=1))
+
+
+@pytest.mark.parametrize("k", [10, 100, 1000])
+def test_one_step_csr_c3(torch_cuda, O, k):
+    cfg = inputs.config("c3", k=k)
+    err = _one_step_case(O, "csr", cfg["n"], O.CSR, rp=cfg["row_ptr"], col=cfg["col"], w=cfg["w"], warm=5)
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+def test_one_step_csr_empty_rows_and_split(torch_cuda, O):
+    n = 1000
+    rp, col = inputs.random_symmetric_csr(n, 2, 5)      # many isolated cells
+    w = np.full(len(col), 0.05, np.float32)
+    for flags in (ion.FLAG_KAHAN, ion.FLAG_KAHAN | ion.FLAG_SPLIT):
+        err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, flags=flags)
+        assert err.max() <= STEP_RTOL
+
+
+def test_one_step_no_gj(torch_cuda, O):
+    err = _one_step_case(O, "nogj", 777, O.NOGJ)
+    assert err.max() <= STEP_RTOL
+
+
+# ------------------------------------------------------------------ trajectories
+
+def _run_both(O, cfg, n_steps, chunk, kind="dense", trace=False, **kw):
+    """Run GPU and oracle side by side in chunks; yield (t, gpu_state, oracle_state)."""
+    n = cfg["n"]
+    S0 = initial_state(O, cfg)
+    k_or = O.DENSE if cfg["kind"] == "dense" else O.CSR
+    ikind = ion.DENSE_UNIFORM if cfg["kind"] == "dense" else ion.CSR
+    Sref = S0.astype(np.float64)
+    sim = ion.Simulation(n, ikind, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"), col=cfg.get("col"),
+                         w=cfg.get("w"), init_state=S0, **kw)
+    if cfg.get("pulses") is not None:
+        sim.set_input(cfg["pulses"])
+    wd = None if cfg.get("w") is None else cfg["w"].astype(np.float64)
+    t = 0
+    try:
+        while t < n_steps:
+            c = min(chunk, n_steps - t)
+            sim.step(c)
+            Sref, tr = O.run(Sref, c, kind=k_or, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"), col=cfg.get("col"),
+                             w=wd, t0=t, pulses=cfg.get("pulses"), trace_cells=np.arange(n) if trace else None,
+                             threads=_threads(O))
+            t += c
+            yield t, sim, Sref, tr
+    finally:
+        sim.close()
+
+
+def test_c1_voltages_within_0p1mv_over_100ms(torch_cuda, O):
+    cfg = inputs.config("c1")
+    worst = 0.0
+    for t, sim, Sref, _ in _run_both(O, cfg, 2000, 100):
+        got = sim.state()
+        worst = max(worst, np.abs(got[:3] - Sref[:3]).max())
+    assert worst <= TRAJ_MV, worst
+
+
+def test_c1_spike_times_over_1s(torch_cuda, O):
+    cfg = inputs.config("c1")
+    n = cfg["n"]
+    S0 = initial_state(O, cfg)
+    _, otr = O.run(S0.astype(np.float64), 20000, kind=O.DENSE, g=cfg["g"], pulses=cfg["pulses"],
+                   trace_cells=np.arange(n), threads=_threads(O))
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=cfg["g"], init_state=S0) as sim:
+        sim.set_input(cfg["pulses"])
+        ion.ion_set_trace(sim.h, 1, 20000)
+        sim.step(20000)
+        gtr = ion.ion_read_trace(sim.h, n, 20000)
+    assert gtr.shape == otr.shape
+    for c in range(n):
+        a = O.spike_steps(gtr[:, c])
+        b = O.spike_steps(otr[:, c])
+        assert len(a) == len(b), (c, a, b)
+        assert np.all(np.abs(a - b) <= 1), (c, a, b)
+
+
+def test_validation_experiment_spikes(torch_cuda, O):
+    """Sec. 3: identical cells + a pulse to all: every cell spikes, in step, on the GPU as
+    in the oracle (spike times within one step), and the GPU cells stay bitwise equal."""
+    cfg = inputs.config("validation")
+    n = cfg["n"]
+    S0 = initial_state(O, cfg)
+    Sref, otr = O.run(S0.astype(np.float64), 4000, kind=O.DENSE, g=cfg["g"], pulses=cfg["pulses"],
+                      trace_cells=np.arange(n), threads=_threads(O))
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=cfg["g"], init_state=S0) as sim:
+        sim.set_input(cfg["pulses"])
+        ion.ion_set_trace(sim.h, 1, 4000)
+        sim.step(4000)
+        gtr = ion.ion_read_trace(sim.h, n, 4000)
+        S = sim.state()
+    assert np.all(S == S[:, :1])
+    a = O.spike_steps(gtr[:, 0])
+    b = O.spike_steps(otr[:, 0])
+    assert len(a) >= 2 and len(a) == len(b) and np.all(np.abs(a - b) <= 1), (a, b)
+
+
+def test_c2_first_20ms(torch_cuda, O):
+    """8192-cell all-to-all network, checked against the FP64 oracle on its first 20 ms."""
+    cfg = inputs.config("c2")
+    worst = 0.0
+    for t, sim, Sref, _ in _run_both(O, cfg, 400, 100):
+        got = sim.state()
+        worst = max(worst, np.abs(got[:3] - Sref[:3]).max())
+    assert worst <= TRAJ_MV, worst
+
+
+@pytest.mark.parametrize("k", [10, 100])
+def test_c3_trajectory(torch_cuda, O, k):
+    cfg = inputs.config("c3", k=k)
+    worst = 0.0
+    for t, sim, Sref, _ in _run_both(O, cfg, 300, 100):
+        got = sim.state()
+        worst = max(worst, np.abs(got[:3] - Sref[:3]).max())
+    assert worst <= TRAJ_MV, worst
+
+
+# ------------------------------------------------------------------ runtime behaviour
+
+def test_graph_replay_bitwise_equals_direct_launches(torch_cuda, O):
+    cfg = inputs.config("c1")
+    S0 = initial_state(O, cfg)
+    out = []
+    for flags in (ion.FLAG_KAHAN, ion.FLAG_KAHAN | ion.FLAG_NO_GRAPH):
+        with ion.Simulation(64, ion.DENSE_UNIFORM, g=cfg["g"], init_state=S0, flags=flags, graph_steps=40) as sim:
+            sim.set_input(cfg["pulses"])
+            sim.step(2123)
+            out.append(sim.state())
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_checkpoint_restart_bitwise(torch_cuda, O):
+    """2n steps straight == n steps, save (state + step count), restore in a new handle, n steps."""
+    cfg = inputs.config("c3", k=10)
+    S0 = initial_state(O, cfg)
+    kw = dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
+    with ion.Simulation(cfg["n"], ion.CSR, init_state=S0, **kw) as a:
+        a.set_input(cfg["pulses"])
+        a.step(1101)
+        mid, t_mid = a.state(), a.t
+        a.step(1100)
+        straight = a.state()
+    with ion.Simulation(cfg["n"], ion.CSR, init_state=mid, **kw) as b:
+        ion.ion_set_step_count(b.h, t_mid)
+        b.set_input(cfg["pulses"])
+        b.step(1100)
+        resumed = b.state()
+    np.testing.assert_array_equal(straight, resumed)
+
+
+def test_nonfinite_state_is_reported(torch_cuda, O):
+    n = 8
+    S0 = O.default_state(n).astype(np.float32)
+    with ion.Simulation(n, ion.NO_GJ, init_state=S0) as sim:
+        sim.set_input(inputs.pulses(np.arange(n), 0.0, 50.0, 5000.0))   # drives explicit Euler to overflow
+        sim.step(1000)
+        with pytest.raises(ion.IonError) as ei:
+            sim.sync()
+        assert ei.value.status == ion.ERR_NONFINITE
+
+
+def test_write_then_read_roundtrip(torch_cuda, O):
+    n = 333
+    S = initial_state(O, dict(n=n, jitter=inputs.vdend_jitter(n, 3)))
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=0.01) as sim:
+        sim.step(3)                 # odd step count: V_dend lives in the second slot
+        sim.write(S)
+        np.testing.assert_array_equal(sim.state(), S)
+        sim.write(S[5] * 0 + 0.25, field=5)
+        assert np.all(sim.state(5) == 0.25)
