@@ -87,7 +87,9 @@ enum ion_mem { ION_HOST = 0, ION_DEVICE = 1 };
 
 enum ion_flag {
     ION_FLAG_KAHAN = 1u << 0,      /* compensated dense gap-junction sums (default on)     */
-    ION_FLAG_PERSISTENT = 1u << 1, /* keep state on chip across steps where it fits        */
+    ION_FLAG_PERSISTENT = 1u << 1, /* dense: one cooperative launch per ion_step call, state in
+                                      registers, bounded grid barrier per step (if every CTA
+                                      fits on the GPU at once; else per-step launches)        */
     ION_FLAG_SURROGATE = 1u << 2,  /* MLP surrogate for the channel rate functions         */
     ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
     ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
@@ -129,6 +131,9 @@ typedef struct {
     void *cuda_stream;          /* cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream;
                                    NULL: the handle creates and owns a non-blocking stream  */
     const void *tune;           /* ion_tune* launch shape override, NULL = built-in choice */
+    int64_t debug_delay_ns;     /* test hook, 0 in production: with ION_FLAG_PERSISTENT one CTA
+                                   sleeps this long before its first grid barrier (a short
+                                   barrier_timeout_ns then yields ION_ERR_TIMEOUT)          */
 } ion_params;
 
 /* Evoked input (Sec. 2.2: one evoked-input word per cell per step).
@@ -152,7 +157,7 @@ typedef struct {
 /* Launch-shape override (filled by the autotuner, or by hand). 0 = choose. */
 typedef struct {
     int32_t dense_rows_per_warp; /* 1, 2, 4, 6 or 8                                 */
-    int32_t dense_warps;         /* warps per CTA, 1..16                            */
+    int32_t dense_warps;         /* warps per CTA, 1..24 (even: two column splits)  */
     int32_t csr_lanes_per_row;   /* 1, 2, 4, 8, 16 or 32                            */
     int32_t csr_rows_per_cta;    /* 32..1024, multiple of 32                        */
     int32_t batch_tile_pairs;    /* work per batched tile, in pair evaluations      */

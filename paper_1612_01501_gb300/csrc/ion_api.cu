@@ -180,26 +180,35 @@ static int num_sms() {
     return sms;
 }
 
-// Dense: pick R rows per warp and W warps per CTA to minimise the rows the busiest SM
-// processes, ceil(grid / SMs) * W * R (every row costs the same N pair evaluations),
-// preferring more warps (latency hiding) and then larger R (fewer shared loads).
+// Dense: a CTA has W warps = GR row groups x GJ column splits (GJ = 2 when W is even)
+// and owns GR * R rows.  Pick (R, W) to minimise the work of the busiest SM,
+// ceil(grid / SMs) * (GR * R + 4): every row costs the same N pair evaluations and every
+// CTA pays about four rows' worth for staging and scaling its V_dend tiles; among equal
+// costs prefer 16..24 warps per CTA (latency hiding without starving registers), then
+// larger R (fewer shared loads per pair).
 void ion_choose_dense_shape(int n, int sms, int *R_out, int *W_out) {
     static const int Rs[] = {8, 6, 4, 2, 1};
     long best_cost = -1;
+    int best_score = -1;
     int bR = 1, bW = 4;
     for (int R : Rs)
-        for (int W = 4; W <= 16; ++W) {
-            const long rows = (long)W * R;
-            const long grid = (n + rows - 1) / rows;
-            const long cost = ((grid + sms - 1) / sms) * rows;
-            const bool better = best_cost < 0 || cost < best_cost ||
-                                (cost == best_cost && (grid <= sms ? W > bW : false));
-            if (better) {
-                best_cost = cost;
-                bR = R;
-                bW = W;
+        for (int GR = 1; GR <= 16; ++GR)
+            for (int GJ = 1; GJ <= 2; ++GJ) {
+                const int W = GR * GJ;
+                if (GJ == 1 && W % 2 == 0) continue;   // even W always means two column splits
+                if (W > 24) continue;                  // 768 threads at most (register budget)
+                const long rows = (long)GR * R;
+                const long grid = (n + rows - 1) / rows;
+                const long cost = ((grid + sms - 1) / sms) * (rows + 4);
+                const int warps_score = (W >= 16 && W <= 24) ? 2 : (W >= 8 ? 1 : 0);
+                const int score = warps_score * 16 + R;
+                if (best_cost < 0 || cost < best_cost || (cost == best_cost && score > best_score)) {
+                    best_cost = cost;
+                    best_score = score;
+                    bR = R;
+                    bW = W;
+                }
             }
-        }
     *R_out = bR;
     *W_out = bW;
 }
@@ -330,7 +339,7 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         if (tu && tu->dense_warps > 0) W = tu->dense_warps;
         if (R != 1 && R != 2 && R != 4 && R != 6 && R != 8)
             return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense_rows_per_warp %d unsupported", R));
-        if (W < 1 || W > 16) return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense_warps %d out of range", W));
+        if (W < 1 || W > 24) return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense_warps %d out of range", W));
         s->dense_R = R;
         s->dense_W = W;
         e = prepare_dense_step(R, W, s->n_pad);
@@ -606,7 +615,7 @@ extern "C" ion_status ion_step(ion_sim *s, int64_t n_steps, const ion_input *inp
         ion_status st = s->prepare_hook(s);
         if (st != ION_OK) return st;
     }
-    if (s->run_override) {
+    if (s->run_override && iapp == nullptr) {
         ion_status st = s->run_override(s, n_steps, iapp);
         if (st != ION_OK) return st;
         s->t += n_steps;

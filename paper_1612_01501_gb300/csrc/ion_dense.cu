@@ -1,85 +1,179 @@
-// ion_dense.cu -- dense all-to-all gap-junction step (Algorithm 1 with C = 100 %).
+// ion_dense.cu -- dense all-to-all gap-junction step (Algorithm 1 with C = 100 %), one
+// launch per step or one persistent launch for many steps.
 //
 // For a uniform pair weight g the gap current of cell i is
 //   Ic_i = g sum_j (0.8 e^{-dV_ij^2/100} + 0.2) dV_ij,  dV_ij = V_i - V_j   (j = 0..N-1).
-// With u = s V, s = sqrt(log2(e)/100), the exponential is 2^{-(u_i-u_j)^2} (one SFU ex2),
-// and the linear part sums in closed form: sum_j dV_ij = N V_i - sum_j V_j.  So
-//   Ic_i = (g/s) [0.8 sum_j 2^{-du^2} du + 0.2 (N u_i - sum_j u_j)],  du = u_i - u_j,
-// and each pair costs one FADD, one FMUL, one ex2 and one FFMA.
+// With m a per-step shift (V_dend of cell 0) and u = s (V - m), s = sqrt(log2(e)/100),
+// the exponential is 2^{-(u_i-u_j)^2} (one SFU ex2) and the linear part sums in closed
+// form, sum_j dV_ij = (N u_i - sum_j u_j) / s.  So
+//   Ic_i = (g/s) [0.8 sum_j 2^{-du^2} du + 0.2 (N u_i - sum_j u_j)],  du = u_i - u_j.
+// The shift keeps the rounding error of du proportional to |V - m| rather than |V|, so
+// nearly synchronous cells keep their relative accuracy.
 //
-// Layout of one launch (N-body style): V_dend(t) is staged into shared memory in tiles
-// of TJ floats by 1-D bulk async copies (cp.async.bulk, completion on an mbarrier),
-// double-buffered when N > TJ.  A CTA owns W*R consecutive rows; each warp owns R of
-// them and each lane walks the tile 4 columns at a time (one 16-byte shared load feeds
-// 4 x R pairs).  Lane sums are folded into Kahan-compensated accumulators every 64
-// columns; after the last tile the 32 lane partials of each row go to shared memory
-// and the thread that updates the row sums them (again compensated) in a fixed order,
-// so results are deterministic.  The fused variant then runs the explicit-Euler cell
-// update of the CTA's rows (one thread per row) and writes V_dend(t+1) to the other
-// buffer, so one launch is one whole step.
+// Layout (N-body style): V_dend(t) is staged into shared memory in tiles of TJ floats by
+// 1-D bulk async copies (cp.async.bulk, completion on an mbarrier), double-buffered when
+// N > TJ, then centred, scaled and negated in place (the tile holds -u_j).  A CTA has
+// GR x GJ warps: GR row groups of R rows and GJ interleaved column splits.  Each lane
+// holds u_i of its R rows and walks its columns four at a time (one 16-byte shared load
+// feeds 4 x R pairs); pairs go two at a time through packed f32x2 arithmetic (per two
+// pairs: one FADD2, one FMUL2, two ex2, one FFMA2).  Lane sums are folded into Kahan-
+// compensated accumulators every 64 columns, then summed pairwise across lanes (a fixed
+// butterfly) and across column splits, so results are deterministic.  The fused step
+// then runs the explicit-Euler cell update of the CTA's rows (one thread per row) and
+// writes V_dend(t+1) to the other V_dend buffer.
 #include <cuda_runtime.h>
 
+#include "ion_async.cuh"
 #include "ion_kernels.cuh"
 
 namespace ion {
 
-// ---- mbarrier + bulk-copy helpers (sm_90+ PTX) ------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+constexpr float PAD_U = 1.0e6f;   // |u| of padded columns: 2^{-PAD_U^2} is exactly 0
+
+struct DenseSmem {
+    float *tile0;     // buffer b at tile0 + b * buf_len
+    int buf_len;
+    int n_tiles;
+    float *part;      // [rows_cta][GJ] row sums per column split
+};
+
+__device__ __forceinline__ DenseSmem dense_smem(unsigned char *raw, int n_pad) {
+    DenseSmem s;
+    s.tile0 = reinterpret_cast<float *>(raw);
+    s.n_tiles = (n_pad + TJ - 1) / TJ;
+    s.buf_len = s.n_tiles > 1 ? TJ : n_pad;
+    s.part = s.tile0 + (s.n_tiles > 1 ? 2 * TJ : n_pad);
+    return s;
 }
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+
+// Issue the bulk copy of tile k (thread 0 only).
+__device__ __forceinline__ void issue_tile(const DenseSmem &sm, const float *src, int n_pad, int k, uint64_t *bar) {
+    const int len = min(TJ, n_pad - k * TJ);
+    mbar_expect_tx(&bar[k & 1], (uint32_t)len * 4u);
+    bulk_g2s(sm.tile0 + (k & 1) * sm.buf_len, src + (int64_t)k * TJ, (uint32_t)len * 4u, &bar[k & 1]);
 }
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// Bounded wait on an mbarrier phase: gives up after ~0.5 s (then flags ST_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
-    if (mbar_try_wait(bar, phase)) return true;
-    const uint64_t t0 = globaltimer_ns();
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        if (mbar_try_wait(bar, phase)) return true;
-        if ((it & 255u) == 255u && globaltimer_ns() - t0 > 500000000ull) break;
+
+// One pass over all columns.  If `src` is non-NULL the first two tiles must already be in
+// flight (issue_tile) and the remaining ones are issued here; if NULL the single tile
+// already holds raw V_dend (single-CTA persistent mode).  On return tot[r] holds this
+// lane's compensated column sum for row r, and (Us, Uc) this thread's share of
+// sum_j u_j.  bar_uses counts completed phases of each mbarrier.  Returns false (in
+// every thread) if a bulk copy did not land in time.
+template <int R, int GJ>
+__device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, int n, int n_pad, uint64_t *bar,
+                                        uint32_t (&bar_uses)[2], float m_shift, const float (&ui)[R], int cs,
+                                        int lane, int kahan, float (&tot)[R], float &Us, float &Uc) {
+    float ks[R], kc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) ks[r] = kc[r] = 0.0f;
+    Us = Uc = 0.0f;
+    for (int kt = 0; kt < sm.n_tiles; ++kt) {
+        const int b = kt & 1;
+        const int j0 = kt * TJ;
+        const int len = min(TJ, n_pad - j0);
+        if (src != nullptr) {
+            const bool landed = mbar_wait_bounded(&bar[b], bar_uses[b] & 1u);
+            bar_uses[b]++;
+            if (__syncthreads_or(!landed)) return false;   // block-uniform decision
+        }
+        float *tb = sm.tile0 + b * sm.buf_len;
+        for (int j = threadIdx.x; j < len; j += blockDim.x) {
+            const bool real = j0 + j < n;
+            const float u = (tb[j] - m_shift) * GJ_SCALE;
+            tb[j] = real ? -u : -PAD_U;
+            if (real) kahan_add(Us, Uc, u);
+        }
+        __syncthreads();
+        const float4 *t4 = reinterpret_cast<const float4 *>(tb);
+        const int n4 = len >> 2;             // float4 columns; len is a multiple of 256
+        constexpr int BLK = 16;              // float4 loads per lane between Kahan folds
+        for (int m0 = cs * 32 + lane; m0 < n4; m0 += 32 * GJ * BLK) {
+            float2 acc[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+            for (int mm = 0; mm < BLK; ++mm) {
+                const int m = m0 + mm * 32 * GJ;
+                if (m < n4) {
+                    const float4 v = t4[m];
+                    const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float2 u2 = make_float2(ui[r], ui[r]);
+                        const float2 da = __fadd2_rn(u2, va);
+                        const float2 db = __fadd2_rn(u2, vb);
+                        const float2 qa = __fmul2_rn(da, da);
+                        const float2 qb = __fmul2_rn(db, db);
+                        const float2 ea = make_float2(ex2_approx(-qa.x), ex2_approx(-qa.y));
+                        const float2 eb = make_float2(ex2_approx(-qb.x), ex2_approx(-qb.y));
+                        acc[r] = __ffma2_rn(ea, da, acc[r]);
+                        acc[r] = __ffma2_rn(eb, db, acc[r]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const float blk = acc[r].x + acc[r].y;
+                if (kahan) kahan_add(ks[r], kc[r], blk);
+                else ks[r] += blk;
+            }
+        }
+        // order this thread's generic accesses of the buffer before any later bulk refill
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();   // every thread is done with this buffer
+        if (src != nullptr && threadIdx.x == 0 && kt + 2 < sm.n_tiles) {
+            issue_tile(sm, src, n_pad, kt + 2, bar);
+        }
     }
-    return mbar_try_wait(bar, phase);
-}
-// 1-D bulk copy global -> shared, completion counted in bytes on `bar`
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
+#pragma unroll
+    for (int r = 0; r < R; ++r) tot[r] = ks[r] - kc[r];
+    return true;
 }
 
-__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
-    const float y = x - comp;
-    const float t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
+// Reduce the lane sums into part[row][split] and the block's sum_j u_j (returned).
+template <int R, int GJ>
+__device__ __forceinline__ float gj_reduce(const DenseSmem &sm, const float (&tot)[R], float Us, float Uc, int rg,
+                                           int cs, int lane, float *red_s, float *red_c, float *U_sh) {
+    const int warp = threadIdx.x >> 5, W = blockDim.x >> 5;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float v = tot[r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) sm.part[(rg * R + r) * GJ + cs] = v;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        Us += __shfl_xor_sync(0xffffffffu, Us, off);
+        Uc += __shfl_xor_sync(0xffffffffu, Uc, off);
+    }
+    if (lane == 0) {
+        red_s[warp] = Us;
+        red_c[warp] = Uc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f, cc = 0.0f;
+        for (int w = 0; w < W; ++w) kahan_add(s, cc, red_s[w] - red_c[w]);
+        *U_sh = s - cc;
+    }
+    __syncthreads();
+    return *U_sh;
 }
 
-// ---- the kernel -------------------------------------------------------------------
-template <int R>
-__global__ void __launch_bounds__(512) dense_step_kernel(const DenseArgs a) {
+// Gap current of local row rr (after gj_reduce).
+template <int GJ>
+__device__ __forceinline__ float row_current(const DenseSmem &sm, int rr, float u_i, int n, float U, float g) {
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < GJ; ++k) S += sm.part[rr * GJ + k];
+    const float lin = fmaf((float)n, u_i, -U);
+    return g * (1.0f / GJ_SCALE) * fmaf(0.8f, S, 0.2f * lin);
+}
+
+// ---- one launch per step ----------------------------------------------------------------
+template <int R, int GJ>
+__global__ void __launch_bounds__(768) dense_step_kernel(const DenseArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red_s[32], red_c[32];
@@ -88,18 +182,17 @@ __global__ void __launch_bounds__(512) dense_step_kernel(const DenseArgs a) {
     const StepCommon &c = a.c;
     const int n = c.n;
     const int W = blockDim.x >> 5;
+    const int GR = W / GJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rows_cta = W * R;
-    const int n_tiles = (c.n_pad + TJ - 1) / TJ;
-    const int buf_len = n_tiles > 1 ? TJ : c.n_pad;
-    float *const tile0 = reinterpret_cast<float *>(smem_raw);    // buffer b at tile0 + b * buf_len
-    float *part_s = tile0 + (n_tiles > 1 ? 2 * TJ : c.n_pad);    // [rows_cta][33]
-    float *part_c = part_s + rows_cta * 33;
+    const int rg = warp % GR, cs = warp / GR;
+    const int rows_cta = GR * R;
+    const DenseSmem sm = dense_smem(smem_raw, c.n_pad);
 
     const int64_t t = step_index(c);
     const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
     float *vnext = a.fuse ? vd_next(c, t) : nullptr;
     const int row_base = blockIdx.x * rows_cta;
+    const float m_shift = vcur[0];
 
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -107,130 +200,31 @@ __global__ void __launch_bounds__(512) dense_step_kernel(const DenseArgs a) {
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < 2 && k < n_tiles; ++k) {
-            const int len = min(TJ, c.n_pad - k * TJ);
-            mbar_expect_tx(&bar[k], (uint32_t)len * 4u);
-            bulk_g2s(tile0 + k * buf_len, vcur + (int64_t)k * TJ, (uint32_t)len * 4u, &bar[k]);
-        }
-    }
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 2 && k < sm.n_tiles; ++k) issue_tile(sm, vcur, c.n_pad, k, bar);
 
-    // rows of this lane (scaled voltages), read directly from global memory
     float ui[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int i = row_base + warp * R + r;
-        ui[r] = (i < n) ? vcur[i] * GJ_SCALE : 0.0f;
+        const int i = row_base + rg * R + r;
+        ui[r] = (i < n) ? (vcur[i] - m_shift) * GJ_SCALE : 0.0f;
     }
-    float ks[R], kc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) ks[r] = kc[r] = 0.0f;
-    float Us = 0.0f, Uc = 0.0f;   // this thread's share of sum_j u_j (compensated)
-
-    bool ok = true;
-    for (int kt = 0; kt < n_tiles; ++kt) {
-        const int b = kt & 1;
-        const int j0 = kt * TJ;
-        const int len = min(TJ, c.n_pad - j0);
-        const bool landed = mbar_wait_bounded(&bar[b], (uint32_t)((kt >> 1) & 1));
-        if (__syncthreads_or(!landed)) {   // block-uniform decision
-            ok = false;
-            break;
-        }
-        // scale the tile in place and accumulate this thread's part of sum_j u_j
-        float *tb = tile0 + b * buf_len;
-        for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            const float u = tb[j] * GJ_SCALE;
-            tb[j] = u;
-            if (j0 + j < n) kahan_add(Us, Uc, u);
-        }
-        __syncthreads();
-        const float4 *t4 = reinterpret_cast<const float4 *>(tb);
-        const int n4 = len >> 2;             // float4 columns; len is a multiple of 256
-        for (int m0 = lane; m0 < n4; m0 += 32 * 16) {
-            float acc[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = 0.0f;
-#pragma unroll 4
-            for (int mm = 0; mm < 16; ++mm) {
-                const int m = m0 + mm * 32;
-                if (m < n4) {
-                    const float4 v = t4[m];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float d0 = ui[r] - v.x, d1 = ui[r] - v.y, d2 = ui[r] - v.z, d3 = ui[r] - v.w;
-                        acc[r] = fmaf(ex2_approx(-d0 * d0), d0, acc[r]);
-                        acc[r] = fmaf(ex2_approx(-d1 * d1), d1, acc[r]);
-                        acc[r] = fmaf(ex2_approx(-d2 * d2), d2, acc[r]);
-                        acc[r] = fmaf(ex2_approx(-d3 * d3), d3, acc[r]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (a.kahan) kahan_add(ks[r], kc[r], acc[r]);
-                else ks[r] += acc[r];
-            }
-        }
-        __syncthreads();   // every thread is done with this buffer
-        if (threadIdx.x == 0 && kt + 2 < n_tiles) {
-            // order this CTA's generic-proxy accesses of the buffer before the async refill
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const int len2 = min(TJ, c.n_pad - (kt + 2) * TJ);
-            mbar_expect_tx(&bar[b], (uint32_t)len2 * 4u);
-            bulk_g2s(tb, vcur + (int64_t)(kt + 2) * TJ, (uint32_t)len2 * 4u, &bar[b]);
-        }
-    }
-    if (!ok) {
+    uint32_t uses[2] = {0u, 0u};
+    float tot[R], Us, Uc;
+    if (!gj_pass<R, GJ>(sm, vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan, tot, Us, Uc)) {
         if (threadIdx.x == 0) {
             atomicOr(c.status, (uint32_t)ST_TIMEOUT);
             // let any copy still in flight land before the CTA's shared memory is released
-            for (int k = 0; k < 2 && k < n_tiles; ++k) (void)mbar_wait_bounded(&bar[k], 0);
+            for (int k = 0; k < 2 && k < sm.n_tiles; ++k) (void)mbar_wait_bounded(&bar[k], uses[k] & 1u);
         }
         return;
     }
-
-    // lane partials of each row -> shared memory
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        part_s[(warp * R + r) * 33 + lane] = ks[r];
-        part_c[(warp * R + r) * 33 + lane] = kc[r];
-    }
-    // sum_j u_j: warp partials (plain shuffle sum of the compensated thread sums is
-    // carried as separate sum / compensation channels), then warp 0 finishes
-    float s1 = Us, c1 = Uc;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        s1 += __shfl_xor_sync(0xffffffffu, s1, off);
-        c1 += __shfl_xor_sync(0xffffffffu, c1, off);
-    }
-    if (lane == 0) {
-        red_s[warp] = s1;
-        red_c[warp] = c1;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f, cc = 0.0f;
-        for (int w = 0; w < W; ++w) kahan_add(s, cc, red_s[w] - red_c[w]);
-        U_sh = s - cc;
-    }
-    __syncthreads();
-    const float U = U_sh;
-    const float g_over_s = a.g * (1.0f / GJ_SCALE);
+    const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, cs, lane, red_s, red_c, &U_sh);
 
     for (int rr = threadIdx.x; rr < rows_cta; rr += blockDim.x) {
         const int i = row_base + rr;
         if (i >= n) break;
-        float s = 0.0f, cc = 0.0f;
-#pragma unroll 8
-        for (int l = 0; l < 32; ++l) {
-            kahan_add(s, cc, part_s[rr * 33 + l]);
-            kahan_add(s, cc, -part_c[rr * 33 + l]);
-        }
-        const float S = s - cc;
-        const float u_i = vcur[i] * GJ_SCALE;
-        const float lin = fmaf((float)n, u_i, -U);
-        const float ic = g_over_s * fmaf(0.8f, S, 0.2f * lin);
+        const float ic = row_current<GJ>(sm, rr, (vcur[i] - m_shift) * GJ_SCALE, n, U, a.g);
         if (!a.fuse) {
             a.ic_out[i] = ic;
             continue;
@@ -243,25 +237,214 @@ __global__ void __launch_bounds__(512) dense_step_kernel(const DenseArgs a) {
     }
 }
 
+// ---- persistent: many steps in one cooperative launch ------------------------------------
+// Each row thread keeps its cell's state in registers across steps.  After the cell
+// update the new V_dend goes to the other global V_dend buffer and the CTAs meet at a
+// bounded grid barrier before staging it for the next step.  With a single CTA and a
+// single tile (small networks) V_dend never leaves shared memory: the row threads
+// write V_dend(t+1) straight into the tile.
+template <int R, int GJ>
+__global__ void __launch_bounds__(576) dense_persist_kernel(const PersistArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float red_s[32], red_c[32];
+    __shared__ float U_sh, m_sh;
+    __shared__ int ok_sh;
+
+    const StepCommon &c = a.c;
+    const int n = c.n;
+    const int W = blockDim.x >> 5;
+    const int GR = W / GJ;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int rg = warp % GR, cs = warp / GR;
+    const int rows_cta = GR * R;
+    const DenseSmem sm = dense_smem(smem_raw, c.n_pad);
+    const bool single = gridDim.x == 1 && sm.n_tiles == 1;
+    const int row_base = blockIdx.x * rows_cta;
+    const int64_t t0 = *c.t_dev;
+
+    // row thread: state of one cell in registers
+    const int my_row = row_base + (int)threadIdx.x;
+    const bool row_thread = threadIdx.x < rows_cta && my_row < n;
+    Cell cell{};
+    float o_ms = 0.0f, o_ma = 0.0f, o_icah = 0.0f, o_ic = 0.0f;   // last step's output-only words
+    int32_t p0 = 0, p1 = 0;
+    if (row_thread) {
+        cell = load_cell(c.S, vd_slot(c.S, t0), my_row);
+        if (c.pulses.off != nullptr) {
+            p0 = c.pulses.off[my_row];
+            p1 = c.pulses.off[my_row + 1];
+        }
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t uses[2] = {0u, 0u};
+    if (single && threadIdx.x == 0) issue_tile(sm, vd_slot(c.S, t0), c.n_pad, 0, bar);
+    if (single) {   // wait for the one initial copy; afterwards the tile is updated in place
+        const bool landed = mbar_wait_bounded(&bar[0], 0u);
+        uses[0] = 1;
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+            return;
+        }
+    }
+    if (a.debug_delay_ns > 0 && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+        const uint64_t d0 = globaltimer_ns();
+        while (globaltimer_ns() - d0 < (uint64_t)a.debug_delay_ns) __nanosleep(1000);
+    }
+
+    bool ok = true;
+    for (int k = 0; k < a.n_steps && ok; ++k) {
+        const int64_t t = t0 + k;
+        const float *vcur = vd_slot(c.S, t);
+        if (!single && threadIdx.x == 0)
+            for (int q = 0; q < 2 && q < sm.n_tiles; ++q) issue_tile(sm, vcur, c.n_pad, q, bar);
+        // shift m = V_dend of cell 0 at step t (from L2, or from the tile itself)
+        if (threadIdx.x == 0) m_sh = single ? sm.tile0[0] : __ldcg(vcur);
+        __syncthreads();
+        const float m_shift = m_sh;
+        float ui[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int i = row_base + rg * R + r;
+            ui[r] = (i < n) ? ((single ? sm.tile0[i] : __ldcg(vcur + i)) - m_shift) * GJ_SCALE : 0.0f;
+        }
+        __syncthreads();   // the in-place scaling below overwrites the tile the loads above read
+        float tot[R], Us, Uc;
+        if (!gj_pass<R, GJ>(sm, single ? nullptr : vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan, tot,
+                            Us, Uc)) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+                atomicExch(a.abort_flag, 1u);
+                for (int q = 0; q < 2 && q < sm.n_tiles; ++q) (void)mbar_wait_bounded(&bar[q], uses[q] & 1u);
+            }
+            ok = false;
+            break;
+        }
+        const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, cs, lane, red_s, red_c, &U_sh);
+        if (row_thread) {
+            const float u_i = (cell.vd - m_shift) * GJ_SCALE;
+            const float ic = row_current<GJ>(sm, (int)threadIdx.x, u_i, n, U, a.g);
+            float iapp = 0.0f;
+            for (int32_t p = p0; p < p1; ++p)
+                if (t >= c.pulses.begin[p] && t < c.pulses.end[p]) iapp += c.pulses.amp[p];
+            const CellNext o = cell_step(c.P, cell, ic, iapp);
+            cell.vd = o.vd; cell.vs = o.vs; cell.va = o.va; cell.ca = o.ca;
+            cell.r = o.r; cell.s = o.s; cell.q = o.q; cell.k = o.k; cell.l = o.l;
+            cell.hs = o.hs; cell.ns = o.ns; cell.xs = o.xs; cell.ha = o.ha; cell.xa = o.xa;
+            o_ms = o.ms; o_ma = o.ma; o_icah = o.icah; o_ic = o.ic;
+            if (!cell_finite(o)) atomicOr(c.status, (uint32_t)ST_NONFINITE);
+            if (c.trace != nullptr && ((t + 1) % c.trace_stride) == 0) {
+                const int64_t sample = (t + 1) / c.trace_stride - 1;
+                c.trace[(sample % c.trace_cap) * (int64_t)n + my_row] = o.va;
+            }
+        }
+        if (single) {
+            __syncthreads();                          // all pair loops are done with the tile
+            if (row_thread) sm.tile0[my_row] = cell.vd;
+            __syncthreads();
+        } else {
+            if (row_thread) vd_slot(c.S, t + 1)[my_row] = cell.vd;
+            ok = grid_barrier(a.bar_count, a.abort_flag, (uint32_t)(k + 1) * gridDim.x, a.timeout_ns, c.status,
+                              &ok_sh);
+        }
+    }
+    // write the final state (after an aborted run: the last completed step)
+    if (row_thread && a.n_steps > 0) {
+        const CellNext o{cell.vd, cell.vs, cell.va, cell.ca, cell.r, cell.s, cell.q, cell.k, cell.l, o_ms,
+                         cell.hs, cell.ns, cell.xs, o_ma, cell.ha, cell.xa, o_icah, o_ic};
+        store_cell(c.S, vd_slot(c.S, t0 + a.n_steps), my_row, o);
+    }
+}
+
 size_t dense_smem_bytes(int n_pad, int R, int W) {
     const int n_tiles = (n_pad + TJ - 1) / TJ;
     const size_t tiles = (n_tiles > 1 ? 2 * TJ : n_pad) * sizeof(float);
-    return tiles + 2 * (size_t)W * R * 33 * sizeof(float);
+    return tiles + (size_t)W * R * sizeof(float);   // part[rows_cta][GJ] = (W / GJ) * R * GJ floats
 }
 
-template <int R>
-static cudaError_t launch_dense_R(const DenseArgs &a, int W, cudaStream_t st) {
-    const int rows_cta = W * R;
+// The launch shape is (R rows per warp, W warps); W = GR * GJ with GJ = 2 column splits
+// when W is even, else 1.
+template <int R, int GJ>
+static cudaError_t launch_dense_RG(const DenseArgs &a, int W, cudaStream_t st) {
+    const int rows_cta = (W / GJ) * R;
     const int grid = (a.c.n + rows_cta - 1) / rows_cta;
     const size_t smem = dense_smem_bytes(a.c.n_pad, R, W);
-    dense_step_kernel<R><<<grid, W * 32, smem, st>>>(a);
+    dense_step_kernel<R, GJ><<<grid, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
+template <int R>
+static cudaError_t launch_dense_R(const DenseArgs &a, int W, cudaStream_t st) {
+    return (W % 2 == 0) ? launch_dense_RG<R, 2>(a, W, st) : launch_dense_RG<R, 1>(a, W, st);
+}
 
+cudaError_t launch_dense_step(const DenseArgs &a, int R, int W, cudaStream_t st) {
+    if (W < 1 || W > 24) return cudaErrorInvalidValue;
+    switch (R) {
+        case 1: return launch_dense_R<1>(a, W, st);
+        case 2: return launch_dense_R<2>(a, W, st);
+        case 4: return launch_dense_R<4>(a, W, st);
+        case 6: return launch_dense_R<6>(a, W, st);
+        case 8: return launch_dense_R<8>(a, W, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R, int GJ>
+static cudaError_t persist_RG(const PersistArgs &a, int W, int *grid_out, bool launch, cudaStream_t st) {
+    const int rows_cta = (W / GJ) * R;
+    const int grid = (a.c.n + rows_cta - 1) / rows_cta;
+    const size_t smem = dense_smem_bytes(a.c.n_pad, R, W);
+    if (!launch) {   // report whether every CTA can be resident at once
+        cudaError_t e = cudaFuncSetAttribute(dense_persist_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0, dev = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_persist_kernel<R, GJ>, W * 32, smem);
+        if (e != cudaSuccess) return e;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        *grid_out = (grid <= per_sm * sms) ? grid : -grid;
+        return cudaSuccess;
+    }
+    void *args[] = {const_cast<PersistArgs *>(&a)};
+    return cudaLaunchCooperativeKernel((const void *)dense_persist_kernel<R, GJ>, dim3(grid), dim3(W * 32), args, smem,
+                                       st);
+}
+template <int R>
+static cudaError_t persist_R(const PersistArgs &a, int W, int GJ, int *g, bool launch, cudaStream_t st) {
+    return (GJ == 2) ? persist_RG<R, 2>(a, W, g, launch, st) : persist_RG<R, 1>(a, W, g, launch, st);
+}
+
+// launch == false: prepare and check only; *grid_out = grid if every CTA can be resident,
+// else -grid.  launch == true: cooperative launch on `st`.  W warps = (W / GJ) row groups
+// x GJ column splits (GJ = 1 or 2, W a multiple of GJ).
+cudaError_t persist_dense(const PersistArgs &a, int R, int W, int GJ, int *grid_out, bool launch, cudaStream_t st) {
+    if (W < 1 || W > 18 || (GJ != 1 && GJ != 2) || W % GJ != 0) return cudaErrorInvalidValue;
+    int dummy = 0;
+    if (!grid_out) grid_out = &dummy;
+    switch (R) {
+        case 1: return persist_R<1>(a, W, GJ, grid_out, launch, st);
+        case 2: return persist_R<2>(a, W, GJ, grid_out, launch, st);
+        case 4: return persist_R<4>(a, W, GJ, grid_out, launch, st);
+        case 6: return persist_R<6>(a, W, GJ, grid_out, launch, st);
+        case 8: return persist_R<8>(a, W, GJ, grid_out, launch, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int R, int GJ>
+static cudaError_t prepare_dense_RG(int W, int n_pad) {
+    const size_t smem = dense_smem_bytes(n_pad, R, W);
+    return cudaFuncSetAttribute(dense_step_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
 template <int R>
 static cudaError_t prepare_dense_R(int W, int n_pad) {
-    const size_t smem = dense_smem_bytes(n_pad, R, W);
-    return cudaFuncSetAttribute(dense_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return (W % 2 == 0) ? prepare_dense_RG<R, 2>(W, n_pad) : prepare_dense_RG<R, 1>(W, n_pad);
 }
 
 // Raise the kernel's dynamic shared-memory limit (done once, outside stream capture).
@@ -276,16 +459,5 @@ cudaError_t prepare_dense_step(int R, int W, int n_pad) {
     }
 }
 int dense_max_rows_per_warp() { return 8; }
-
-cudaError_t launch_dense_step(const DenseArgs &a, int R, int W, cudaStream_t st) {
-    switch (R) {
-        case 1: return launch_dense_R<1>(a, W, st);
-        case 2: return launch_dense_R<2>(a, W, st);
-        case 4: return launch_dense_R<4>(a, W, st);
-        case 6: return launch_dense_R<6>(a, W, st);
-        case 8: return launch_dense_R<8>(a, W, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
 
 }  // namespace ion

@@ -1,13 +1,81 @@
-// ion_ext.cu -- per-flag extensions of a simulation handle (persistent, surrogate) and
-// the batched / training entry points.
+// ion_ext.cu -- per-flag extensions of a simulation handle (persistent dense launches,
+// surrogate) and the batched / training entry points.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "ion.h"
 #include "ion_sim.h"
 
+using namespace ion;
+
+// ---- persistent dense launches ----------------------------------------------------------
+static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
+    (void)iapp;
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 24);
+        PersistArgs a{};
+        a.c = ion_step_common(s, 0, nullptr);
+        a.g = s->g;
+        a.n_steps = chunk;
+        a.kahan = 1;
+        a.bar_count = s->d_bar;
+        a.abort_flag = s->d_bar + 1;
+        a.timeout_ns = s->barrier_timeout_ns;
+        a.debug_delay_ns = s->debug_delay_ns;
+        cudaError_t e = cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(uint32_t), s->st);
+        if (e == cudaSuccess) e = persist_dense(a, s->persist_R, s->persist_W, s->persist_GJ, nullptr, true, s->st);
+        s->launches++;
+        if (e == cudaSuccess) e = launch_advance(s->d_t, chunk, s->st);
+        s->launches++;
+        if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "persistent launch: %s", cudaGetErrorString(e));
+        done += chunk;
+    }
+    return ION_OK;
+}
+
+// Shape of a persistent launch: one CTA of ceil(n / 8) warps (8 rows each, one column
+// split) when n <= 144, so small networks keep V_dend in shared memory; else the
+// per-step shape, if all its CTAs can be resident at once.
+static bool choose_persist_shape(ion_sim *s) {
+    PersistArgs probe{};
+    probe.c.n = s->n;
+    probe.c.n_pad = s->n_pad;
+    int R, W, GJ;
+    if (s->n <= 144) {
+        R = 8;
+        W = (s->n + 7) / 8;
+        GJ = 1;
+    } else {
+        R = s->dense_R;
+        W = s->dense_W;
+        GJ = (W % 2 == 0) ? 2 : 1;
+    }
+    int grid = 0;
+    if (persist_dense(probe, R, W, GJ, &grid, false, s->st) != cudaSuccess || grid <= 0) return false;
+    s->persist_R = R;
+    s->persist_W = W;
+    s->persist_GJ = GJ;
+    return true;
+}
+
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
-    (void)p;
+    s->debug_delay_ns = p->debug_delay_ns;
     if (s->flags & ION_FLAG_SURROGATE) return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "surrogate: not built");
+    if ((s->flags & ION_FLAG_PERSISTENT) && s->kind == ION_DENSE_UNIFORM && !(s->flags & ION_FLAG_SPLIT)) {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+        if (coop && choose_persist_shape(s)) {
+            if (cudaMalloc(&s->d_bar, 2 * sizeof(uint32_t)) != cudaSuccess)
+                return ion_fail(nullptr, ION_ERR_OOM, "persistent: barrier allocation failed");
+            s->run_override = persist_run;
+            s->extra_free = [](ion_sim *q) {
+                cudaFree(q->d_bar);
+                q->d_bar = nullptr;
+            };
+        }
+    }
     return ION_OK;
 }
 

@@ -76,6 +76,16 @@ struct CsrArgs {
     float *ic_out;
     const float *vd_in;
 };
+struct PersistArgs {
+    StepCommon c;         // k_off unused: the launch runs steps *t_dev .. *t_dev + n_steps - 1
+    float g;
+    int32_t n_steps;
+    int32_t kahan;
+    uint32_t *bar_count;  // grid-barrier arrivals (zeroed before the launch)
+    uint32_t *abort_flag; // set by a CTA whose wait timed out (zeroed before the launch)
+    uint64_t timeout_ns;  // bound on one grid-barrier wait
+    int64_t debug_delay_ns;  // test hook: the last CTA sleeps this long before its first step
+};
 struct CellArgs {
     StepCommon c;
     const float *ic;      // NULL: no gap current
@@ -91,6 +101,8 @@ cudaError_t launch_rates(float V, float ca, float *xinf_tau /*24 floats, device*
 cudaError_t launch_default_state(const ModelF &P, float V0, float ca0, float gcal, int32_t n, int64_t stride,
                                  float *state, cudaStream_t st);
 cudaError_t prepare_dense_step(int rows_per_warp, int warps, int n_pad);
+cudaError_t persist_dense(const PersistArgs &a, int rows_per_warp, int warps, int col_splits, int *grid_out,
+                          bool launch, cudaStream_t st);
 int dense_max_rows_per_warp();
 
 // shared-memory size of a dense launch

@@ -45,6 +45,9 @@ struct ion_sim {
     uint32_t flags = 0;
     int32_t graph_steps = 50, check_every = 64;
     uint64_t barrier_timeout_ns = 0;
+    int64_t debug_delay_ns = 0;
+    uint32_t *d_bar = nullptr;      // grid barrier counter + abort word (persistent launches)
+    int persist_R = 0, persist_W = 0, persist_GJ = 1;
     int device = 0, sms = 1;
     int dense_R = 1, dense_W = 4, csr_SW = 8, csr_rows = 256;
     cudaGraphExec_t gexec = nullptr;

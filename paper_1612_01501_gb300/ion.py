@@ -59,7 +59,7 @@ class ion_params(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("model", ctypes.POINTER(ion_model)), ("flags", ctypes.c_uint32),
                 ("surrogate", ctypes.c_void_p), ("check_every", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
                 ("barrier_timeout_ns", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("tune", ctypes.c_void_p)]
+                ("tune", ctypes.c_void_p), ("debug_delay_ns", ctypes.c_int64)]
 
 
 class ion_input(ctypes.Structure):
@@ -210,7 +210,7 @@ def _conn_struct(kind, g=0.0, row_ptr=None, col=None, w=None):
 
 
 def _params_struct(dt_ms=0.05, model=None, flags=FLAG_KAHAN, stream=None, graph_steps=0, tune=None,
-                   surrogate=None, check_every=0, barrier_timeout_ns=0):
+                   surrogate=None, check_every=0, barrier_timeout_ns=0, debug_delay_ns=0):
     p = ion_params()
     p.dt_ms = float(dt_ms)
     m = _model_struct(model)
@@ -219,6 +219,7 @@ def _params_struct(dt_ms=0.05, model=None, flags=FLAG_KAHAN, stream=None, graph_
     p.graph_steps = int(graph_steps)
     p.check_every = int(check_every)
     p.barrier_timeout_ns = int(barrier_timeout_ns)
+    p.debug_delay_ns = int(debug_delay_ns)
     p.cuda_stream = ctypes.c_void_p(stream) if stream else None
     keep = [m]
     if tune is not None:

@@ -18,11 +18,29 @@ def initial_state(O, cfg, model=None):
     return S.astype(np.float32)
 
 
-def step_rel_err(S_gpu, S_ref):
+def step_rel_err(S_gpu, S_ref, ic_scale=None):
+    """|S_gpu - S_ref| / max(|S_ref|, floor) per field and cell.
+
+    The gap current I_c is a sum of terms of both signs that can cancel; its error is
+    measured against the scale of its terms, ic_scale_i = sum_j w_ij |dV_ij| (when
+    given), the quantity the FP32 rounding of the individual terms is proportional to.
+    """
     S_gpu = np.asarray(S_gpu, np.float64)
     S_ref = np.asarray(S_ref, np.float64)
     den = np.maximum(np.abs(S_ref), FLOORS[:, None])
+    if ic_scale is not None:
+        den[18] = np.maximum(den[18], np.asarray(ic_scale, np.float64))
     return np.abs(S_gpu - S_ref) / den
+
+
+def csr_abs_scale(row_ptr, col, w, vd):
+    """sum_{e in row i} w_e |V_i - V_col(e)| for every row i."""
+    n = len(row_ptr) - 1
+    vd = np.asarray(vd, np.float64)
+    rows = np.repeat(np.arange(n), np.diff(row_ptr))
+    if len(col) == 0:
+        return np.zeros(n)
+    return np.bincount(rows, weights=np.asarray(w, np.float64) * np.abs(vd[rows] - vd[col]), minlength=n)
 
 
 def sum_abs_dv(vd):

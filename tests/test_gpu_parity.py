@@ -11,7 +11,7 @@ import pytest
 from paper_1612_01501_gb300 import inputs
 from paper_1612_01501_gb300 import ion
 
-from helpers import STEP_RTOL, TRAJ_MV, initial_state, step_rel_err, sum_abs_dv
+from helpers import STEP_RTOL, TRAJ_MV, csr_abs_scale, initial_state, step_rel_err, sum_abs_dv
 
 pytestmark = pytest.mark.gpu
 
@@ -104,8 +104,13 @@ def _one_step_case(O, name, n, kind, g=0.0, rp=None, col=None, w=None, warm=50, 
     with ion.Simulation(n, ikind, g=g, row_ptr=rp, col=col, w=w, init_state=Sw32, **kw) as sim:
         sim.step(1, dense=iapp[None, :])
         got = sim.state()
-    err = step_rel_err(got, ref)
-    return err
+    if kind == O.DENSE:
+        scale = g * sum_abs_dv(Sw32[0])
+    elif kind == O.CSR:
+        scale = csr_abs_scale(rp, col, w, Sw32[0])
+    else:
+        scale = None
+    return step_rel_err(got, ref, scale)
 
 
 @pytest.mark.parametrize("n", [1, 64, 300, 8192])
