@@ -156,8 +156,11 @@ typedef struct {
 
 /* Launch-shape override (filled by the autotuner, or by hand). 0 = choose. */
 typedef struct {
-    int32_t dense_rows_per_warp; /* 1, 2, 4, 6 or 8                                 */
-    int32_t dense_warps;         /* warps per CTA, 1..24 (even: two column splits)  */
+    int32_t dense_rows_per_warp; /* R: 1, 2, 4, 6 or 8                              */
+    int32_t dense_warps;         /* W warps per CTA (<= 1024 threads for R <= 2,
+                                    768 otherwise), a multiple of dense_col_splits */
+    int32_t dense_col_splits;    /* GJ: 1, 2 or 4 warps share a row group, each
+                                    taking every GJ-th group of 128 columns         */
     int32_t csr_lanes_per_row;   /* 1, 2, 4, 8, 16 or 32                            */
     int32_t csr_rows_per_cta;    /* 32..1024, multiple of 32                        */
     int32_t batch_tile_pairs;    /* work per batched tile, in pair evaluations      */

@@ -180,37 +180,40 @@ static int num_sms() {
     return sms;
 }
 
-// Dense: a CTA has W warps = GR row groups x GJ column splits (GJ = 2 when W is even)
-// and owns GR * R rows.  Pick (R, W) to minimise the work of the busiest SM,
+// Dense: a CTA has W = GR x GJ warps (GR row groups of R rows, GJ column splits) and
+// owns GR * R rows.  Pick (R, GR, GJ) to minimise the work of the busiest SM,
 // ceil(grid / SMs) * (GR * R + 4): every row costs the same N pair evaluations and every
-// CTA pays about four rows' worth for staging and scaling its V_dend tiles; among equal
-// costs prefer 16..24 warps per CTA (latency hiding without starving registers), then
-// larger R (fewer shared loads per pair).
-void ion_choose_dense_shape(int n, int sms, int *R_out, int *W_out) {
-    static const int Rs[] = {8, 6, 4, 2, 1};
+// CTA pays about four rows' worth for staging and scaling its V_dend tiles.  Among equal
+// costs prefer 24..32 warps per CTA (the SFU pipe needs that many warps in flight; a
+// probe of the pair loop gave 0.44 / 0.67 / 0.77 of the ex2 peak at 9 / 18 / 32 warps),
+// then fewer rows per warp (a smaller register footprint).
+void ion_choose_dense_shape(int n, int sms, int *R_out, int *W_out, int *GJ_out) {
+    static const int Rs[] = {1, 2, 4, 6, 8};
+    static const int GJs[] = {1, 2, 4};
     long best_cost = -1;
     int best_score = -1;
-    int bR = 1, bW = 4;
+    int bR = 1, bW = 1, bGJ = 1;
     for (int R : Rs)
-        for (int GR = 1; GR <= 16; ++GR)
-            for (int GJ = 1; GJ <= 2; ++GJ) {
+        for (int GJ : GJs)
+            for (int GR = 1; GR <= 32; ++GR) {
                 const int W = GR * GJ;
-                if (GJ == 1 && W % 2 == 0) continue;   // even W always means two column splits
-                if (W > 24) continue;                  // 768 threads at most (register budget)
+                if (W * 32 > dense_max_threads(R)) continue;
                 const long rows = (long)GR * R;
                 const long grid = (n + rows - 1) / rows;
                 const long cost = ((grid + sms - 1) / sms) * (rows + 4);
-                const int warps_score = (W >= 16 && W <= 24) ? 2 : (W >= 8 ? 1 : 0);
-                const int score = warps_score * 16 + R;
+                const int warps_score = (W >= 24) ? 3 : (W >= 16 ? 2 : (W >= 8 ? 1 : 0));
+                const int score = warps_score * 16 + (8 - R);
                 if (best_cost < 0 || cost < best_cost || (cost == best_cost && score > best_score)) {
                     best_cost = cost;
                     best_score = score;
                     bR = R;
                     bW = W;
+                    bGJ = GJ;
                 }
             }
     *R_out = bR;
     *W_out = bW;
+    *GJ_out = bGJ;
 }
 
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
@@ -332,17 +335,20 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     // connectivity
     if (s->kind == ION_DENSE_UNIFORM) {
         s->g = conn->g_c;
-        int R, W;
-        ion_choose_dense_shape(s->n, sms, &R, &W);
+        int R, W, GJ;
+        ion_choose_dense_shape(s->n, sms, &R, &W, &GJ);
         const ion_tune *tu = (const ion_tune *)params->tune;
         if (tu && tu->dense_rows_per_warp > 0) R = tu->dense_rows_per_warp;
         if (tu && tu->dense_warps > 0) W = tu->dense_warps;
+        if (tu && tu->dense_col_splits > 0) GJ = tu->dense_col_splits;
         if (R != 1 && R != 2 && R != 4 && R != 6 && R != 8)
             return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense_rows_per_warp %d unsupported", R));
-        if (W < 1 || W > 24) return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense_warps %d out of range", W));
+        if ((GJ != 1 && GJ != 2 && GJ != 4) || W < 1 || W % GJ != 0 || W * 32 > dense_max_threads(R))
+            return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense shape R=%d W=%d GJ=%d unsupported", R, W, GJ));
         s->dense_R = R;
         s->dense_W = W;
-        e = prepare_dense_step(R, W, s->n_pad);
+        s->dense_GJ = GJ;
+        e = prepare_dense_step(R, W, GJ, s->n_pad);
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: dense setup: %s", cudaGetErrorString(e)));
     } else if (s->kind == ION_CSR) {
         s->g = conn->g_c;
@@ -506,7 +512,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
         a.fuse = split ? 0 : 1;
         a.ic_out = s->d_ic;
         a.vd_in = nullptr;
-        e = launch_dense_step(a, s->dense_R, s->dense_W, s->st);
+        e = launch_dense_step(a, s->dense_R, s->dense_W, s->dense_GJ, s->st);
         s->launches++;
         if (e == cudaSuccess && split) {
             CellArgs ca{c, s->d_ic};
@@ -786,9 +792,9 @@ extern "C" ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, flo
     ION_CK(nullptr, cudaMallocAsync(&pad, (size_t)n_pad * sizeof(float), st));
     cudaError_t e = cudaMemcpyAsync(pad, vdend, (size_t)n * sizeof(float), cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = launch_fill(pad + n, PAD_VOLT, n_pad - n, st);
-    int R, W;
-    ion_choose_dense_shape(n, num_sms(), &R, &W);
-    if (e == cudaSuccess) e = prepare_dense_step(R, W, n_pad);
+    int R, W, GJ;
+    ion_choose_dense_shape(n, num_sms(), &R, &W, &GJ);
+    if (e == cudaSuccess) e = prepare_dense_step(R, W, GJ, n_pad);
     if (e == cudaSuccess) {
         DenseArgs a{};
         a.c.n = n;
@@ -798,7 +804,7 @@ extern "C" ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, flo
         a.fuse = 0;
         a.ic_out = ic;
         a.vd_in = pad;
-        e = launch_dense_step(a, R, W, st);
+        e = launch_dense_step(a, R, W, GJ, st);
     }
     cudaError_t e2 = cudaFreeAsync(pad, st);
     if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "ion_gj_dense: %s", cudaGetErrorString(e));

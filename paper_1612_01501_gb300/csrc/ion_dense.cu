@@ -172,8 +172,14 @@ __device__ __forceinline__ float row_current(const DenseSmem &sm, int rr, float 
 }
 
 // ---- one launch per step ----------------------------------------------------------------
+// Launch bounds: up to 1024 threads (64 registers) when R <= 2, else 768.
+template <int R>
+struct DenseBounds {
+    static constexpr int threads = R <= 2 ? 1024 : 768;
+};
+
 template <int R, int GJ>
-__global__ void __launch_bounds__(768) dense_step_kernel(const DenseArgs a) {
+__global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(const DenseArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red_s[32], red_c[32];
@@ -243,8 +249,15 @@ __global__ void __launch_bounds__(768) dense_step_kernel(const DenseArgs a) {
 // bounded grid barrier before staging it for the next step.  With a single CTA and a
 // single tile (small networks) V_dend never leaves shared memory: the row threads
 // write V_dend(t+1) straight into the tile.
+// Launch bounds of the persistent variant (it also keeps a cell's state in registers):
+// 896 threads (72 registers) when R <= 2, else 576.
+template <int R>
+struct PersistBounds {
+    static constexpr int threads = R <= 2 ? 896 : 576;
+};
+
 template <int R, int GJ>
-__global__ void __launch_bounds__(576) dense_persist_kernel(const PersistArgs a) {
+__global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kernel(const PersistArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ float red_s[32], red_c[32];
@@ -367,97 +380,104 @@ size_t dense_smem_bytes(int n_pad, int R, int W) {
     return tiles + (size_t)W * R * sizeof(float);   // part[rows_cta][GJ] = (W / GJ) * R * GJ floats
 }
 
-// The launch shape is (R rows per warp, W warps); W = GR * GJ with GJ = 2 column splits
-// when W is even, else 1.
-template <int R, int GJ>
-static cudaError_t launch_dense_RG(const DenseArgs &a, int W, cudaStream_t st) {
-    const int rows_cta = (W / GJ) * R;
-    const int grid = (a.c.n + rows_cta - 1) / rows_cta;
-    const size_t smem = dense_smem_bytes(a.c.n_pad, R, W);
-    dense_step_kernel<R, GJ><<<grid, W * 32, smem, st>>>(a);
-    return cudaGetLastError();
+// ---- launch-shape dispatch: R rows per warp, W warps = (W / GJ) row groups x GJ splits ----
+template <template <int, int> class Op, int R>
+static cudaError_t dispatch_gj(int GJ, typename Op<R, 1>::Args &args) {
+    switch (GJ) {
+        case 1: return Op<R, 1>::run(args);
+        case 2: return Op<R, 2>::run(args);
+        case 4: return Op<R, 4>::run(args);
+        default: return cudaErrorInvalidValue;
+    }
 }
-template <int R>
-static cudaError_t launch_dense_R(const DenseArgs &a, int W, cudaStream_t st) {
-    return (W % 2 == 0) ? launch_dense_RG<R, 2>(a, W, st) : launch_dense_RG<R, 1>(a, W, st);
-}
-
-cudaError_t launch_dense_step(const DenseArgs &a, int R, int W, cudaStream_t st) {
-    if (W < 1 || W > 24) return cudaErrorInvalidValue;
+template <template <int, int> class Op>
+static cudaError_t dispatch(int R, int GJ, typename Op<1, 1>::Args &args) {
     switch (R) {
-        case 1: return launch_dense_R<1>(a, W, st);
-        case 2: return launch_dense_R<2>(a, W, st);
-        case 4: return launch_dense_R<4>(a, W, st);
-        case 6: return launch_dense_R<6>(a, W, st);
-        case 8: return launch_dense_R<8>(a, W, st);
+        case 1: return dispatch_gj<Op, 1>(GJ, args);
+        case 2: return dispatch_gj<Op, 2>(GJ, args);
+        case 4: return dispatch_gj<Op, 4>(GJ, args);
+        case 6: return dispatch_gj<Op, 6>(GJ, args);
+        case 8: return dispatch_gj<Op, 8>(GJ, args);
         default: return cudaErrorInvalidValue;
     }
 }
 
+struct StepLaunch {
+    const DenseArgs *a;
+    int W;
+    cudaStream_t st;
+    bool prepare_only;
+};
 template <int R, int GJ>
-static cudaError_t persist_RG(const PersistArgs &a, int W, int *grid_out, bool launch, cudaStream_t st) {
-    const int rows_cta = (W / GJ) * R;
-    const int grid = (a.c.n + rows_cta - 1) / rows_cta;
-    const size_t smem = dense_smem_bytes(a.c.n_pad, R, W);
-    if (!launch) {   // report whether every CTA can be resident at once
-        cudaError_t e = cudaFuncSetAttribute(dense_persist_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 0, dev = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_persist_kernel<R, GJ>, W * 32, smem);
-        if (e != cudaSuccess) return e;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        *grid_out = (grid <= per_sm * sms) ? grid : -grid;
-        return cudaSuccess;
+struct StepOp {
+    using Args = StepLaunch;
+    static cudaError_t run(StepLaunch &L) {
+        if (L.W % GJ != 0 || L.W * 32 > DenseBounds<R>::threads) return cudaErrorInvalidValue;
+        const int rows_cta = (L.W / GJ) * R;
+        const size_t smem = dense_smem_bytes(L.a->c.n_pad, R, L.W);
+        if (L.prepare_only)
+            return cudaFuncSetAttribute(dense_step_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const int grid = (L.a->c.n + rows_cta - 1) / rows_cta;
+        dense_step_kernel<R, GJ><<<grid, L.W * 32, smem, L.st>>>(*L.a);
+        return cudaGetLastError();
     }
-    void *args[] = {const_cast<PersistArgs *>(&a)};
-    return cudaLaunchCooperativeKernel((const void *)dense_persist_kernel<R, GJ>, dim3(grid), dim3(W * 32), args, smem,
-                                       st);
-}
-template <int R>
-static cudaError_t persist_R(const PersistArgs &a, int W, int GJ, int *g, bool launch, cudaStream_t st) {
-    return (GJ == 2) ? persist_RG<R, 2>(a, W, g, launch, st) : persist_RG<R, 1>(a, W, g, launch, st);
-}
+};
 
-// launch == false: prepare and check only; *grid_out = grid if every CTA can be resident,
-// else -grid.  launch == true: cooperative launch on `st`.  W warps = (W / GJ) row groups
-// x GJ column splits (GJ = 1 or 2, W a multiple of GJ).
-cudaError_t persist_dense(const PersistArgs &a, int R, int W, int GJ, int *grid_out, bool launch, cudaStream_t st) {
-    if (W < 1 || W > 18 || (GJ != 1 && GJ != 2) || W % GJ != 0) return cudaErrorInvalidValue;
-    int dummy = 0;
-    if (!grid_out) grid_out = &dummy;
-    switch (R) {
-        case 1: return persist_R<1>(a, W, GJ, grid_out, launch, st);
-        case 2: return persist_R<2>(a, W, GJ, grid_out, launch, st);
-        case 4: return persist_R<4>(a, W, GJ, grid_out, launch, st);
-        case 6: return persist_R<6>(a, W, GJ, grid_out, launch, st);
-        case 8: return persist_R<8>(a, W, GJ, grid_out, launch, st);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
+struct PersistLaunch {
+    const PersistArgs *a;
+    int W;
+    cudaStream_t st;
+    bool launch;
+    int *grid_out;
+};
 template <int R, int GJ>
-static cudaError_t prepare_dense_RG(int W, int n_pad) {
-    const size_t smem = dense_smem_bytes(n_pad, R, W);
-    return cudaFuncSetAttribute(dense_step_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-template <int R>
-static cudaError_t prepare_dense_R(int W, int n_pad) {
-    return (W % 2 == 0) ? prepare_dense_RG<R, 2>(W, n_pad) : prepare_dense_RG<R, 1>(W, n_pad);
+struct PersistOp {
+    using Args = PersistLaunch;
+    static cudaError_t run(PersistLaunch &L) {
+        if (L.W % GJ != 0 || L.W * 32 > PersistBounds<R>::threads) return cudaErrorInvalidValue;
+        const int rows_cta = (L.W / GJ) * R;
+        const int grid = (L.a->c.n + rows_cta - 1) / rows_cta;
+        const size_t smem = dense_smem_bytes(L.a->c.n_pad, R, L.W);
+        if (!L.launch) {   // prepare, and report whether every CTA can be resident at once
+            cudaError_t e = cudaFuncSetAttribute(dense_persist_kernel<R, GJ>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int per_sm = 0, dev = 0, sms = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dense_persist_kernel<R, GJ>, L.W * 32, smem);
+            if (e != cudaSuccess) return e;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            *L.grid_out = (grid <= per_sm * sms) ? grid : -grid;
+            return cudaSuccess;
+        }
+        void *args[] = {const_cast<PersistArgs *>(L.a)};
+        return cudaLaunchCooperativeKernel((const void *)dense_persist_kernel<R, GJ>, dim3(grid), dim3(L.W * 32), args,
+                                           smem, L.st);
+    }
+};
+
+cudaError_t launch_dense_step(const DenseArgs &a, int R, int W, int GJ, cudaStream_t st) {
+    StepLaunch L{&a, W, st, false};
+    return dispatch<StepOp>(R, GJ, L);
 }
 
 // Raise the kernel's dynamic shared-memory limit (done once, outside stream capture).
-cudaError_t prepare_dense_step(int R, int W, int n_pad) {
-    switch (R) {
-        case 1: return prepare_dense_R<1>(W, n_pad);
-        case 2: return prepare_dense_R<2>(W, n_pad);
-        case 4: return prepare_dense_R<4>(W, n_pad);
-        case 6: return prepare_dense_R<6>(W, n_pad);
-        case 8: return prepare_dense_R<8>(W, n_pad);
-        default: return cudaErrorInvalidValue;
-    }
+cudaError_t prepare_dense_step(int R, int W, int GJ, int n_pad) {
+    DenseArgs a{};
+    a.c.n_pad = n_pad;
+    StepLaunch L{&a, W, nullptr, true};
+    return dispatch<StepOp>(R, GJ, L);
 }
-int dense_max_rows_per_warp() { return 8; }
+
+// launch == false: prepare and check only; *grid_out = grid if every CTA can be resident,
+// else -grid.  launch == true: cooperative launch on `st`.
+cudaError_t persist_dense(const PersistArgs &a, int R, int W, int GJ, int *grid_out, bool launch, cudaStream_t st) {
+    int dummy = 0;
+    PersistLaunch L{&a, W, st, launch, grid_out ? grid_out : &dummy};
+    return dispatch<PersistOp>(R, GJ, L);
+}
+
+int dense_max_threads(int R) { return R <= 2 ? 1024 : 768; }
+int persist_max_threads(int R) { return R <= 2 ? 896 : 576; }
 
 }  // namespace ion

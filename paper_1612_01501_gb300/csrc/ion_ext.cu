@@ -37,7 +37,8 @@ static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
 
 // Shape of a persistent launch: one CTA of ceil(n / 8) warps (8 rows each, one column
 // split) when n <= 144, so small networks keep V_dend in shared memory; else the
-// per-step shape, if all its CTAs can be resident at once.
+// per-step shape, if the persistent kernel allows that many threads and all its CTAs
+// can be resident at once.
 static bool choose_persist_shape(ion_sim *s) {
     PersistArgs probe{};
     probe.c.n = s->n;
@@ -50,7 +51,8 @@ static bool choose_persist_shape(ion_sim *s) {
     } else {
         R = s->dense_R;
         W = s->dense_W;
-        GJ = (W % 2 == 0) ? 2 : 1;
+        GJ = s->dense_GJ;
+        if (W * 32 > persist_max_threads(R)) return false;
     }
     int grid = 0;
     if (persist_dense(probe, R, W, GJ, &grid, false, s->st) != cudaSuccess || grid <= 0) return false;

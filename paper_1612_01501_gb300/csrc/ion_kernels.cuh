@@ -92,7 +92,7 @@ struct CellArgs {
 };
 
 // launchers (return the CUDA launch status)
-cudaError_t launch_dense_step(const DenseArgs &a, int rows_per_warp, int warps, cudaStream_t st);
+cudaError_t launch_dense_step(const DenseArgs &a, int rows_per_warp, int warps, int col_splits, cudaStream_t st);
 cudaError_t launch_csr_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, cudaStream_t st);
 cudaError_t launch_cell_step(const CellArgs &a, cudaStream_t st);
 cudaError_t launch_advance(int64_t *t_dev, int64_t k, cudaStream_t st);
@@ -100,10 +100,11 @@ cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);
 cudaError_t launch_rates(float V, float ca, float *xinf_tau /*24 floats, device*/, cudaStream_t st);
 cudaError_t launch_default_state(const ModelF &P, float V0, float ca0, float gcal, int32_t n, int64_t stride,
                                  float *state, cudaStream_t st);
-cudaError_t prepare_dense_step(int rows_per_warp, int warps, int n_pad);
+cudaError_t prepare_dense_step(int rows_per_warp, int warps, int col_splits, int n_pad);
 cudaError_t persist_dense(const PersistArgs &a, int rows_per_warp, int warps, int col_splits, int *grid_out,
                           bool launch, cudaStream_t st);
-int dense_max_rows_per_warp();
+int dense_max_threads(int rows_per_warp);     // thread limit of the step kernel
+int persist_max_threads(int rows_per_warp);   // thread limit of the persistent kernel
 
 // shared-memory size of a dense launch
 size_t dense_smem_bytes(int n_pad, int rows_per_warp, int warps);

@@ -49,7 +49,7 @@ struct ion_sim {
     uint32_t *d_bar = nullptr;      // grid barrier counter + abort word (persistent launches)
     int persist_R = 0, persist_W = 0, persist_GJ = 1;
     int device = 0, sms = 1;
-    int dense_R = 1, dense_W = 4, csr_SW = 8, csr_rows = 256;
+    int dense_R = 1, dense_W = 4, dense_GJ = 1, csr_SW = 8, csr_rows = 256;
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     bool no_graph = false;
@@ -74,7 +74,7 @@ ion::ModelF ion_model_to_f32(const ion_model &m, double dt);
 ion::StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp);
 float *ion_field_ptr(ion_sim *s, int32_t field);
 ion_status ion_validate_csr(int32_t n, const ion_conn *c);
-void ion_choose_dense_shape(int n, int sms, int *R, int *W);
+void ion_choose_dense_shape(int n, int sms, int *R, int *W, int *GJ);
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
 void ion_sim_free_device(ion_sim *s);
 // per-flag setup of the extensions (ion_ext.cu)

@@ -69,7 +69,7 @@ class ion_input(ctypes.Structure):
 
 class ion_tune(ctypes.Structure):
     _fields_ = [("dense_rows_per_warp", ctypes.c_int32), ("dense_warps", ctypes.c_int32),
-                ("csr_lanes_per_row", ctypes.c_int32), ("csr_rows_per_cta", ctypes.c_int32),
+                ("dense_col_splits", ctypes.c_int32), ("csr_lanes_per_row", ctypes.c_int32), ("csr_rows_per_cta", ctypes.c_int32),
                 ("batch_tile_pairs", ctypes.c_int32)]
 
 
