@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     float tot[R], Us, Uc;
     if (!gj_pass<R, GJ>(sm, vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan, tot, Us, Uc)) {
         if (threadIdx.x == 0) {
-            atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+            if (c.status != nullptr) atomicOr(c.status, (uint32_t)ST_TIMEOUT);   // primitives pass none
             // let any copy still in flight land before the CTA's shared memory is released
             for (int k = 0; k < 2 && k < sm.n_tiles; ++k) (void)mbar_wait_bounded(&bar[k], uses[k] & 1u);
         }
