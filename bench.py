@@ -1,12 +1,14 @@
 """Benchmark of the InfOli hot path on one GB300 (or N independent replicas).
 
-Workload (default): the 8192-cell all-to-all network (RGJ at 100 % density), FP32 state
-in SoA layout, g_c = 0.04 / N * 64, V_dend jittered +-5 mV from seed 1, no evoked input;
-one bench step simulates 200 ms = 4000 time steps of 50 us.  Metric: cell-timesteps/s
-(and gap-junction pair evaluations/s, N^2 per time step).
+Default workload: the 8192-cell all-to-all network (RGJ at 100 % density), FP32 state in
+SoA layout, g_c = 0.04 / N * 64, V_dend jittered +-5 mV from seed 1, no evoked input.  One
+bench step simulates 200 ms = 4000 time steps of 50 us from the same initial state.
+Metric: cell-timesteps/s (and gap-junction pair evaluations/s, N^2 per time step).
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead (on a
-bounded sample of the same workload, all host cores).
+`--workload` selects another configuration for a secondary line (c1: 64 dense cells for
+1 s; c3_k10 / c3_k100 / c3_k1000: 65 536 cells with random symmetric CSR connectivity).
+`--impl reference` times the FP64 CPU oracle instead (a bounded sample, all host cores).
+Prints one JSON line.
 """
 from __future__ import annotations
 
@@ -25,10 +27,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "cell-timesteps/s"
-WORKLOAD = "c2_dense_8192_allToAll_200ms"
-N_CELLS = 8192
-STEPS_PER_BENCH_STEP = 4000          # 200 ms of simulated time
 L2_FLUSH_BYTES = 512 << 20           # > 129 MB L2
+WORKLOADS = {
+    "c2": dict(name="c2_dense_8192_allToAll_200ms", cfg="c2", steps=4000),
+    "c1": dict(name="c1_dense_64_allToAll_1s", cfg="c1", steps=20000),
+    "c3_k10": dict(name="c3_csr_65536_k10_200ms", cfg="c3", k=10, steps=4000),
+    "c3_k100": dict(name="c3_csr_65536_k100_200ms", cfg="c3", k=100, steps=4000),
+    "c3_k1000": dict(name="c3_csr_65536_k1000_200ms", cfg="c3", k=1000, steps=4000),
+}
 
 
 def parse():
@@ -37,16 +43,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--sim-steps", type=int, default=STEPS_PER_BENCH_STEP)
-    ap.add_argument("--no-extra", action="store_true", help="skip the secondary configuration lines")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--sim-steps", type=int, default=0, help="time steps per bench step (0: the workload's)")
+    ap.add_argument("--variant", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--no-extra", action="store_true", help="skip the CPU baseline and the e2e leg")
     return ap.parse_args()
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 class Clocks:
@@ -77,70 +82,70 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.p.kill()
         self.f.flush()
-        rows = []
-        for line in open(self.f.name):
-            parts = [x.strip() for x in line.split(",")]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[x.strip() for x in line.split(",")] for line in open(self.f.name)]
+        rows = [r for r in rows if len(r) >= 9]
         os.unlink(self.f.name)
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        num = lambda x: x.replace(".", "").isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
 
 
-def c2_initial_state():
-    """FP32 initial state of the workload, computed by the library on the device."""
-    from paper_1612_01501_gb300 import inputs, ion
-    S = ion.ion_default_state(N_CELLS)
-    S[0] = (S[0].astype(np.float64) + inputs.vdend_jitter(N_CELLS, 1)).astype(np.float32)
-    return S
-
-
-def cpu_baseline(sample_steps: int = 3, reps: int = 1):
-    """FP64 oracle on the host cores: `sample_steps` time steps of the same workload."""
-    import oracle as O
+def load_workload(key):
+    """Input bundle of a workload (seeded, synthetic) as the oracle and the GPU see it."""
     from paper_1612_01501_gb300 import inputs
-    cfg = inputs.config("c2")
-    S = O.default_state(N_CELLS)
+    w = WORKLOADS[key]
+    return inputs.config(w["cfg"], k=w.get("k"))
+
+
+def cpu_baseline(key, sample_steps):
+    """FP64 oracle on all host cores: `sample_steps` time steps of the workload."""
+    import oracle as O
+    cfg = load_workload(key)
+    S = O.default_state(cfg["n"])
     S[O.F["V_dend"]] += cfg["jitter"]
     S = S.astype(np.float32).astype(np.float64)
     threads = O.max_threads()
-    O.run(S, 1, kind=O.DENSE, g=cfg["g"], threads=threads)        # warm caches / thread pool
+    kind = O.DENSE if cfg["kind"] == "dense" else O.CSR
+    kw = dict(kind=kind, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"), col=cfg.get("col"),
+              w=None if cfg.get("w") is None else cfg["w"].astype(np.float64), threads=threads)
+    O.run(S, 1, **kw)        # warm caches and the thread pool
     t0 = time.perf_counter()
-    for _ in range(reps):
-        O.run(S, sample_steps, kind=O.DENSE, g=cfg["g"], threads=threads)
+    O.run(S, sample_steps, **kw)
     dt = time.perf_counter() - t0
-    v = N_CELLS * sample_steps * reps / dt
+    v = cfg["n"] * sample_steps / dt
     return {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"{sample_steps * reps} time steps of the 8192-cell dense network (FP64, OpenMP over cells)",
-            "pair_evals_per_s": v * N_CELLS, "seconds": dt}
+            "sample": f"{sample_steps} time steps of {WORKLOADS[key]['name']} (FP64, OpenMP over cells)",
+            "seconds": dt}
 
 
-def run_reference(args, rank, world):
+def reference_sample_steps(key):
+    return {"c2": 8, "c1": 2000}.get(key, 20)
+
+
+def run_reference(args, rank):
+    """The reference arm: the FP64 oracle on the host cores (rank 0 only)."""
     if rank != 0:
         return 0
-    steps = []
     import oracle as O
     O.build()
-    for k in range(args.warmup + args.steps):
-        r = cpu_baseline(sample_steps=8)
-        if k >= args.warmup:
-            steps.append(r)
-    t = sum(r["seconds"] for r in steps)
-    cells = N_CELLS * 8 * len(steps)
-    v = cells / t
+    k = reference_sample_steps(args.workload)
+    runs = [cpu_baseline(args.workload, k) for _ in range(args.warmup + args.steps)][args.warmup:]
+    t = sum(r["seconds"] for r in runs)
+    n = load_workload(args.workload)["n"]
+    v = n * k * len(runs) / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(steps),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / len(runs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_cells": N_CELLS, "timesteps_per_step": 8,
-                       "note": "bounded sample: 8 time steps per bench step"},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": steps[0]["cores"], "kind": "oracle",
-                             "sample": "8 time steps of the 8192-cell dense network per bench step"},
+            "config": {"workload": WORKLOADS[args.workload]["name"], "n_cells": n, "timesteps_per_step": k,
+                       "note": f"bounded sample: {k} time steps per bench step"},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": runs[0]["cores"], "kind": "oracle",
+                             "sample": f"{k} time steps of {WORKLOADS[args.workload]['name']} per bench step"},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -150,7 +155,7 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
-        return run_reference(args, rank, world)
+        return run_reference(args, rank)
 
     import torch
     torch.cuda.set_device(local)
@@ -158,29 +163,47 @@ def main():
     # (the default stream's handle is 0, which the library reads as "no stream given")
     torch.cuda.set_stream(torch.cuda.Stream())
     from paper_1612_01501_gb300 import build as B
-    if rank == 0 or world == 1:
-        B.build()
     pg = None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
         pg = dist
+        if rank == 0:
+            B.build()
         pg.barrier()
+    else:
         B.build()
-    from paper_1612_01501_gb300 import inputs, ion
+    from paper_1612_01501_gb300 import ion
 
+    key = args.workload
+    wl = WORKLOADS[key]
+    sim_steps = args.sim_steps or wl["steps"]
+    cfg = load_workload(key)
+    n = cfg["n"]
+    dense = cfg["kind"] == "dense"
+    S0 = ion.ion_default_state(n)
+    S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
     stream = torch.cuda.current_stream().cuda_stream
-    S0 = c2_initial_state()
-    g = inputs.junction_weight(0.04, N_CELLS)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
+    def make_sim(flags):
+        kw = dict(g=cfg["g"]) if dense else dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
+        sim = ion.Simulation(n, ion.DENSE_UNIFORM if dense else ion.CSR, init_state=S0, stream=stream,
+                             graph_steps=100, flags=flags, **kw)
+        if cfg.get("pulses") is not None:
+            sim.set_input(cfg["pulses"])
+        return sim
+
+    def reset(sim):
+        sim.write(S0)
+        ion.ion_set_step_count(sim.h, 0)
+
     def measure(flags):
-        """Time args.steps bench steps (4000 time steps each) of one variant."""
-        sim = ion.Simulation(N_CELLS, ion.DENSE_UNIFORM, g=g, init_state=S0, stream=stream, graph_steps=100,
-                             flags=flags)
+        """Time args.steps bench steps of one variant (each from the same state and t = 0)."""
+        sim = make_sim(flags)
         for _ in range(args.warmup):
-            sim.write(S0)
-            sim.step(args.sim_steps)
+            reset(sim)
+            sim.step(sim_steps)
         torch.cuda.synchronize()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         if pg:
@@ -191,9 +214,9 @@ def main():
         launches0 = sim.launches
         for k in range(args.steps):
             flush.fill_(float(k))                       # evict L2 between timed steps
-            sim.write(S0)                               # same initial state every step (untimed)
+            reset(sim)                                  # same initial state every step (untimed)
             ev[k][0].record()
-            sim.step(args.sim_steps)
+            sim.step(sim_steps)
             ev[k][1].record()
         torch.cuda.synchronize()
         ck = clocks.stop()
@@ -206,8 +229,13 @@ def main():
         sim.sync()                                      # the run stayed finite
         return sim, ms, launches, ck
 
+    cand = [("graph", ion.FLAG_KAHAN)]
+    if dense:
+        cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
+    if args.variant != "auto":
+        cand = [c for c in cand if c[0] == args.variant]
     variants = {}
-    for name, flags in (("graph", ion.FLAG_KAHAN), ("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT)):
+    for name, flags in cand:
         sim_v, ms_v, l_v, ck_v = measure(flags)
         variants[name] = dict(sim=sim_v, ms=ms_v, launches=l_v, clocks=ck_v)
     best = min(variants, key=lambda k: variants[k]["ms"])
@@ -216,56 +244,75 @@ def main():
         if k != best:
             v["sim"].close()
 
-    cell_steps = N_CELLS * args.sim_steps * args.steps * world
+    cell_steps = n * sim_steps * args.steps * world
     value = cell_steps / (ms * 1e-3)
-    pair_evals_s = value * N_CELLS
-    # roofline of the dense kernel: SFU-bound, one ex2 per pair evaluation.  The timed
-    # region is (almost) all dense-kernel time: per time step one fused launch (graph
-    # variant) or one slice of the persistent launch.
-    per_step_s = ms * 1e-3 / (args.sim_steps * args.steps)
-    ex2_peak = ion.ion_probe_peak(0, 4096, stream)
-    ffma_peak = ion.ion_probe_peak(1, 4096, stream)
-    achieved_ex2 = N_CELLS * N_CELLS / per_step_s
+    per_step_s = ms * 1e-3 / (sim_steps * args.steps)
+    if dense:
+        # SFU-bound: one ex2 per pair evaluation (N^2 per time step)
+        peak = ion.ion_probe_peak(0, 4096, stream)
+        achieved = n * n / per_step_s
+        roof = {"bound": "alu", "unit": "ex2/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "dense_persist_kernel" if best == "persistent" else "dense_step_kernel",
+                "peak_source": "measured SFU ex2 rate (ion_probe_peak) in the same process",
+                "ffma_peak_per_s": ion.ion_probe_peak(1, 4096, stream), "us_per_timestep": per_step_s * 1e6}
+        extra = {"pair_evals_per_s": value * n}
+    else:
+        # HBM: per time step the CSR (8 B per edge + 4 B per row), the cell state
+        # (15 words read + 18 written) and the pulse offsets (8 B per cell)
+        nnz = len(cfg["col"])
+        bytes_step = 8 * nnz + 4 * (n + 1) + 132 * n + 8 * n
+        achieved = bytes_step / per_step_s / 1e9
+        peak = 6792.4
+        try:
+            peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+        except (OSError, KeyError, ValueError):
+            pass
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "csr_step_kernel", "algorithmic_bytes_per_timestep": bytes_step,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6,
+                "note": "working set fits in L2 (129 MB)" if bytes_step < 100e6 else "streams from HBM"}
+        extra = {"edges_per_s": value / n * nnz, "nnz": nnz}
 
-    # e2e through the public API with pinned host buffers (H2D state in, D2H state out)
-    S_pin = torch.from_numpy(S0.copy()).pin_memory()
-    out_pin = torch.empty_like(S_pin).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        ion.ion_write_state(sim.h, S_pin.numpy())
-        sim.step(args.sim_steps)
-        out_pin.numpy()[:] = ion.ion_read_state(sim.h, N_CELLS)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = N_CELLS * args.sim_steps * e2e_steps * world / e2e_s
-
-    extra = {}
+    line = None
     if rank == 0:
-        cpu = cpu_baseline(sample_steps=3)
         line = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_cells": N_CELLS, "timesteps_per_step": args.sim_steps,
-                       "g_c": g, "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
-            "pair_evals_per_s": pair_evals_s,
-            "roofline": {"bound": "alu", "unit": "ex2/s", "achieved": achieved_ex2, "peak": ex2_peak,
-                         "frac": achieved_ex2 / ex2_peak, "traffic": None,
-                         "kernel": "dense_persist_kernel" if best == "persistent" else "dense_step_kernel",
-                         "peak_source": "measured SFU ex2 probe (ion_probe_peak), same clock",
-                         "ffma_peak_per_s": ffma_peak, "us_per_timestep": per_step_s * 1e6},
+            "config": {"workload": wl["name"], "n_cells": n, "timesteps_per_step": sim_steps,
+                       "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) between timed steps"},
+            "roofline": roof,
             "variants": {k: {"ms_per_step": v["ms"] / args.steps,
                              "cell_timesteps_per_s": cell_steps / (v["ms"] * 1e-3)} for k, v in variants.items()},
             "variant": best,
-            "cpu_baseline": {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": int(S0.nbytes),
-                    "d2h_bytes_per_step": int(S0.nbytes)},
             "gpu_launches": int(launches),
             "clocks": ck,
         }
-        line.update({k: v for k, v in extra.items() if k not in line})
+        line.update(extra)
+    if not args.no_extra:
+        # e2e through the public API with pinned host buffers (H2D state in, D2H state out)
+        S_pin = torch.from_numpy(S0.copy()).pin_memory()
+        out_pin = torch.empty_like(S_pin).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ion.ion_write_state(sim.h, S_pin.numpy())
+            ion.ion_set_step_count(sim.h, 0)
+            sim.step(sim_steps)
+            out_pin.numpy()[:] = ion.ion_read_state(sim.h, n)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([e2e_s], device="cuda")
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        if rank == 0:
+            line["e2e"] = {"value": n * sim_steps * e2e_steps * world / e2e_s, "unit": METRIC,
+                           "h2d_bytes_per_step": int(S0.nbytes), "d2h_bytes_per_step": int(S0.nbytes)}
+            cpu = cpu_baseline(key, reference_sample_steps(key) if key != "c2" else 3)
+            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()
     if pg:

@@ -251,6 +251,27 @@ void ion_destroy(ion_sim *sim);
 ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, float *ic, int32_t kahan,
                         void *cuda_stream);
 
+/* Same currents as ion_gj_dense, computed without allocating any memory.
+ *
+ * The paper has no counterpart of this entry point.  It exists for callers that must not
+ * allocate: a simulation loop with a hard per-step deadline (an allocation can block or
+ * synchronise the device), code running while a stream is being captured into a CUDA
+ * graph, and host programs whose device memory belongs to their own allocator.
+ * ion_gj_dense takes its scratch (V_dend copied and padded to a multiple of 256 floats)
+ * from the stream-ordered allocator; this variant keeps that scratch in a fixed device
+ * array compiled into the library, 65536 floats (256 KiB) on every GPU that loads it,
+ * held until the process exits.  So n rounded up to a multiple of 256 may be at most
+ * 65536; a larger n returns ION_ERR_INVALID_ARG without touching the device.
+ * Arguments, layout and result are those of ion_gj_dense.
+ * The first call on each device looks up the array's device address with that device
+ * current: make that first call before starting any stream capture.
+ * Every call on a device shares the one array and leaves its contents behind; each call
+ * rewrites the whole range it reads, so nothing needs clearing between calls.  Calls
+ * whose work can overlap on the GPU (other streams, other host threads) race on the
+ * array: the caller must order them. */
+ion_status ion_gj_dense_noalloc(const float *vdend, int32_t n, float g_c, float *ic, int32_t kahan,
+                                void *cuda_stream);
+
 /* Ic[i] = sum_{e in row i} w[e] (0.8 e^{-dV^2/100} + 0.2) dV, dV = V_i - V_{col[e]}
  * (Algorithm 1 over a CSR matrix).  All arrays on the device; w NULL means every
  * weight is g_c. */

@@ -111,6 +111,8 @@ _SIGS = {
     "ion_destroy": (None, [ctypes.c_void_p]),
     "ion_gj_dense": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p, ctypes.c_int32,
                                     ctypes.c_void_p]),
+    "ion_gj_dense_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_float, ctypes.c_void_p,
+                                            ctypes.c_int32, ctypes.c_void_p]),
     "ion_gj_csr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_float, ctypes.c_void_p, ctypes.c_void_p]),
     "ion_cell_update": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
@@ -373,6 +375,12 @@ def _stream(stream):
 def ion_gj_dense(vdend, g: float, ic, kahan: bool = True, stream=None):
     _check(lib().ion_gj_dense(vdend.data_ptr(), int(vdend.numel()), float(g), ic.data_ptr(), int(bool(kahan)),
                               _stream(stream)))
+
+
+def ion_gj_dense_noalloc(vdend, g: float, ic, kahan: bool = True, stream=None):
+    """ion_gj_dense without any allocation (fixed scratch array of 65536 floats per device)."""
+    _check(lib().ion_gj_dense_noalloc(vdend.data_ptr(), int(vdend.numel()), float(g), ic.data_ptr(),
+                                      int(bool(kahan)), _stream(stream)))
 
 
 def ion_gj_csr(vdend, row_ptr, col, w, g: float, ic, stream=None):
