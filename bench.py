@@ -34,6 +34,7 @@ WORKLOADS = {
     "c3_k10": dict(name="c3_csr_65536_k10_200ms", cfg="c3", k=10, steps=4000),
     "c3_k100": dict(name="c3_csr_65536_k100_200ms", cfg="c3", k=100, steps=4000),
     "c3_k1000": dict(name="c3_csr_65536_k1000_200ms", cfg="c3", k=1000, steps=4000),
+    "c4": dict(name="c4_batch_256_nets_logU32-4096_half_dense_100ms", cfg="c4", steps=2000),
 }
 
 
@@ -100,6 +101,15 @@ def load_workload(key):
     """Input bundle of a workload (seeded, synthetic) as the oracle and the GPU see it."""
     from paper_1612_01501_gb300 import inputs
     w = WORKLOADS[key]
+    if w["cfg"] == "c4":
+        nets = [inputs.batch_network(sp) for sp in inputs.batch_specs()]
+        off, cells, beg, end, amp = 0, [], [], [], []
+        for b in nets:
+            p = b["pulses"]
+            cells.append(p[0] + off); beg.append(p[1]); end.append(p[2]); amp.append(p[3])
+            off += b["n"]
+        pul = (np.concatenate(cells).astype(np.int32), np.concatenate(beg), np.concatenate(end), np.concatenate(amp))
+        return dict(n=off, kind="batch", nets=nets, jitter=np.concatenate([b["jitter"] for b in nets]), pulses=pul)
     return inputs.config(w["cfg"], k=w.get("k"))
 
 
@@ -107,16 +117,21 @@ def cpu_baseline(key, sample_steps):
     """FP64 oracle on all host cores: `sample_steps` time steps of the workload."""
     import oracle as O
     cfg = load_workload(key)
-    S = O.default_state(cfg["n"])
-    S[O.F["V_dend"]] += cfg["jitter"]
-    S = S.astype(np.float32).astype(np.float64)
     threads = O.max_threads()
-    kind = O.DENSE if cfg["kind"] == "dense" else O.CSR
-    kw = dict(kind=kind, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"), col=cfg.get("col"),
-              w=None if cfg.get("w") is None else cfg["w"].astype(np.float64), threads=threads)
-    O.run(S, 1, **kw)        # warm caches and the thread pool
+    jobs = cfg["nets"] if cfg["kind"] == "batch" else [cfg]
+    runs = []
+    for b in jobs:
+        S = O.default_state(b["n"])
+        S[O.F["V_dend"]] += b["jitter"]
+        S = S.astype(np.float32).astype(np.float64)
+        kind = O.DENSE if b["kind"] == "dense" else O.CSR
+        kw = dict(kind=kind, g=b.get("g", 0.0), row_ptr=b.get("row_ptr"), col=b.get("col"),
+                  w=None if b.get("w") is None else b["w"].astype(np.float64), threads=threads)
+        runs.append((S, kw))
+    O.run(runs[0][0], 1, **runs[0][1])        # warm caches and the thread pool
     t0 = time.perf_counter()
-    O.run(S, sample_steps, **kw)
+    for S, kw in runs:
+        O.run(S, sample_steps, **kw)
     dt = time.perf_counter() - t0
     v = cfg["n"] * sample_steps / dt
     return {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
@@ -125,7 +140,7 @@ def cpu_baseline(key, sample_steps):
 
 
 def reference_sample_steps(key):
-    return {"c2": 8, "c1": 2000}.get(key, 20)
+    return {"c2": 8, "c1": 2000, "c4": 3}.get(key, 20)
 
 
 def run_reference(args, rank):
@@ -181,12 +196,24 @@ def main():
     cfg = load_workload(key)
     n = cfg["n"]
     dense = cfg["kind"] == "dense"
+    batch = cfg["kind"] == "batch"
     S0 = ion.ion_default_state(n)
     S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
+    tune_table = None
     stream = torch.cuda.current_stream().cuda_stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def make_sim(flags):
+        nonlocal tune_table
+        if batch:
+            specs = [dict(n=b["n"], kind=ion.DENSE_UNIFORM, g=b["g"]) if b["kind"] == "dense" else
+                     dict(n=b["n"], kind=ion.CSR, row_ptr=b["row_ptr"], col=b["col"], w=b["w"]) for b in cfg["nets"]]
+            sim = ion.Simulation.__new__(ion.Simulation)
+            sim.n = n
+            sim.h = ion.ion_create_batch(specs, init_state=S0, stream=stream, graph_steps=100, flags=flags)
+            sim.set_input(cfg["pulses"])
+            tune_table = ion.ion_autotune(sim.h, 20)     # project-written autotuner: time the tile shapes
+            return sim
         kw = dict(g=cfg["g"]) if dense else dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
         sim = ion.Simulation(n, ion.DENSE_UNIFORM if dense else ion.CSR, init_state=S0, stream=stream,
                              graph_steps=100, flags=flags, **kw)
@@ -247,7 +274,19 @@ def main():
     cell_steps = n * sim_steps * args.steps * world
     value = cell_steps / (ms * 1e-3)
     per_step_s = ms * 1e-3 / (sim_steps * args.steps)
-    if dense:
+    if batch:
+        # one ex2 per dense pair and per CSR edge; the SFU rate bounds the mix
+        work = sum(b["n"] ** 2 if b["kind"] == "dense" else len(b["col"]) for b in cfg["nets"])
+        peak = ion.ion_probe_peak(0, 4096, stream)
+        achieved = work / per_step_s
+        roof = {"bound": "alu", "unit": "ex2/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "batch_step_kernel",
+                "peak_source": "measured SFU ex2 rate (ion_probe_peak) in the same process",
+                "us_per_timestep": per_step_s * 1e6}
+        extra = {"pair_evals_per_s": sum(b["n"] ** 2 for b in cfg["nets"] if b["kind"] == "dense") / per_step_s,
+                 "edges_per_s": sum(len(b["col"]) for b in cfg["nets"] if b["kind"] == "csr") / per_step_s,
+                 "autotuned": tune_table, "n_networks": len(cfg["nets"])}
+    elif dense:
         # SFU-bound: one ex2 per pair evaluation (N^2 per time step)
         peak = ion.ion_probe_peak(0, 4096, stream)
         achieved = n * n / per_step_s

@@ -154,16 +154,20 @@ typedef struct {
     const float *pulse_amp;
 } ion_input;
 
-/* Launch-shape override (filled by the autotuner, or by hand). 0 = choose. */
+/* Launch-shape override (filled by ion_autotune, or by hand).  0 = the built-in choice. */
 typedef struct {
-    int32_t dense_rows_per_warp; /* R: 1, 2, 4, 6 or 8                              */
+    int32_t dense_rows_per_warp; /* R: 1, 2, 4, 6 or 8 (batches: 1, 2, 4 or 8)      */
     int32_t dense_warps;         /* W warps per CTA (<= 1024 threads for R <= 2,
                                     768 otherwise), a multiple of dense_col_splits */
     int32_t dense_col_splits;    /* GJ: 1, 2 or 4 warps share a row group, each
                                     taking every GJ-th group of 128 columns         */
     int32_t csr_lanes_per_row;   /* 1, 2, 4, 8, 16 or 32                            */
-    int32_t csr_rows_per_cta;    /* 32..1024, multiple of 32                        */
-    int32_t batch_tile_pairs;    /* work per batched tile, in pair evaluations      */
+    int32_t csr_rows_per_cta;    /* rows per CTA of 256 threads, 1..256             */
+    int32_t csr_lanes_scale;     /* batches: 0 = lanes per row from each network's
+                                    mean degree, +1 = twice that, -1 = half        */
+    int32_t csr_staging;         /* single CSR networks: 0 = choose, 1 = gather V_dend
+                                    through L1/L2, 2 = stage V_dend in shared memory
+                                    128 KB at a time (one CTA per SM)                */
 } ion_tune;
 
 typedef struct ion_sim ion_sim;
@@ -190,9 +194,13 @@ ion_status ion_default_state(const ion_model *model, int32_t n, float *out);
 ion_status ion_create(const ion_net *net, const ion_conn *conn, const ion_params *params,
                       const float *init_state, ion_sim **out);
 
-/* Several independent networks advanced together (one launch per step covers all).
- * Cells are numbered consecutively across networks (network b's cell i is global cell
- * offset_b + i); state buffers and pulse cells use the global numbering. */
+/* Several independent networks advanced together: one launch per time step covers all
+ * of them (a list of tiles, each one network's rows), and ion_step replays CUDA graphs of
+ * graph_steps launches.  Cells are numbered consecutively across networks (network b's
+ * cell i is global cell offset_b + i, offset_b = n_0 + ... + n_{b-1}); init_state, the
+ * state read and written, pulse cells and trace samples all use this numbering.
+ * Dense networks may have at most 8192 cells; CSR arrays must be host memory.
+ * ION_FLAG_PERSISTENT, ION_FLAG_SPLIT and ION_FLAG_SURROGATE are not supported here. */
 ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, const ion_conn *conns,
                             const ion_params *params, const float *init_state,
                             ion_sim **out);
@@ -218,7 +226,8 @@ ion_status ion_read_state(ion_sim *sim, int32_t field, float *out, int64_t count
  * the handle's stream after earlier steps. */
 ion_status ion_write_state(ion_sim *sim, int32_t field, const float *in, int64_t count);
 
-/* Device pointer of one field of the current state (valid until the next ion_step). */
+/* Device pointer of one field of the current state (valid until the next ion_step).
+ * Not available for batches (their state is laid out in padded segments). */
 ion_status ion_state_device_ptr(ion_sim *sim, int32_t field, float **out);
 
 /* Record V_axon of every cell every `stride` steps into a device ring of `capacity`
@@ -226,6 +235,14 @@ ion_status ion_state_device_ptr(ion_sim *sim, int32_t field, float **out);
  * (oldest first) to host memory: out[s * n_cells + i]. */
 ion_status ion_set_trace(ion_sim *sim, int32_t stride, int32_t capacity);
 ion_status ion_read_trace(ion_sim *sim, float *out, int64_t max_samples, int64_t *n_written);
+
+/* Time candidate launch shapes on this handle's own network(s), `steps` time steps each,
+ * and keep the fastest (the state and step count are restored afterwards).  Single
+ * dense networks: (R, W, GJ) near the cost model's optimum; single CSR networks: lanes
+ * per row and rows per CTA around the degree-based choice; batches: rows per dense tile,
+ * rows per CSR tile and the lanes-per-row scale.  *chosen (nullable) receives the table.
+ * Not for ION_FLAG_PERSISTENT handles.  Synchronises. */
+ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
 
 /* Steps taken so far (the absolute index of the next step). */
 int64_t ion_step_count(const ion_sim *sim);

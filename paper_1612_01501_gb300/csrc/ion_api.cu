@@ -216,6 +216,9 @@ void ion_choose_dense_shape(int n, int sms, int *R_out, int *W_out, int *GJ_out)
     *GJ_out = bGJ;
 }
 
+// CSR: lanes per row from the mean degree (about two edges per lane per pass, four per
+// lane for the densest rows), and rows per CTA so that a row group's work per CTA stays
+// near 2-8 K edges and the grid has several CTAs per SM.
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
     int sw = 32;
     if (mean_deg <= 3) sw = 1;
@@ -224,7 +227,46 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
     else if (mean_deg <= 40) sw = 8;
     else if (mean_deg <= 120) sw = 16;
     *SW = sw;
-    *rows = 256;
+    int r = 256;
+    if (mean_deg > 48) r = 128;
+    if (mean_deg > 192) r = 64;
+    if (mean_deg > 384) r = 32;
+    *rows = r;
+}
+
+// Shared-memory staging of V_dend for a CSR network (mode 0: choose, 1: off, 2: on).
+// Staging pays once the gathers dominate: on for a mean degree of 32 or more in networks
+// of at least 4096 cells.  One CTA per SM owns ceil(n / SMs) rows (at most 1024).  Only
+// CSR arrays copied from the host are staged: their columns were checked to be sorted
+// and in range, which the chunk boundaries rely on.
+ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
+    const double deg = s->n > 0 ? (double)s->nnz / s->n : 0.0;
+    const bool on = mode == 2 || (mode == 0 && deg >= 32.0 && s->n >= 4096);
+    s->csr_staged = 0;
+    // staging relies on validated (sorted, in-range) columns: host-copied CSR only
+    if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr) return ION_OK;
+    s->n_chunks = (s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK;
+    int rows = (s->n + s->sms - 1) / s->sms;
+    if (rows > 1024) rows = 1024;
+    if (rows < 1) rows = 1;
+    int sw, r_unused;
+    ion_choose_csr_shape(deg / s->n_chunks, &sw, &r_unused);
+    if (s->csr_chunk_rows == 0) s->csr_chunk_rows = rows;
+    s->csr_chunk_SW = sw;
+    if (s->n_chunks > 1 && !s->d_mid) {
+        cudaError_t e = cudaMalloc(&s->d_mid, (size_t)(s->n_chunks - 1) * s->n * sizeof(int32_t));
+        if (e == cudaSuccess) e = launch_csr_chunk_bounds(s->d_rowptr, s->d_col, s->n, s->n_chunks, s->d_mid, s->st);
+        if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
+    }
+    CsrArgs probe{};
+    probe.c.n = s->n;
+    probe.c.n_pad = s->n_pad;
+    probe.col = s->d_col;
+    probe.w = s->d_w;
+    cudaError_t e = launch_csr_chunk_step(probe, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, true, s->st);
+    if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
+    s->csr_staged = 1;
+    return ION_OK;
 }
 
 // ---- creation -------------------------------------------------------------------------
@@ -248,6 +290,7 @@ void ion_sim_free_device(ion_sim *s) {
     cudaFree(s->d_iapp);
     cudaFree(s->d_trace);
     cudaFree(s->d_ic);
+    cudaFree(s->d_mid);
     s->extra_free(s);
 }
 
@@ -282,6 +325,7 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     ion_sim *s = new (std::nothrow) ion_sim();
     if (!s) return ion_fail(nullptr, ION_ERR_OOM, "ion_create: host allocation failed");
     s->n = net->n_cells;
+    s->n_user = net->n_cells;
     s->kind = net->kind;
     s->n_pad = (int32_t)round_up(s->n, PAD_J);
     s->stride = s->n_pad;
@@ -376,10 +420,14 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         const ion_tune *tu = (const ion_tune *)params->tune;
         if (tu && tu->csr_lanes_per_row > 0) SW = tu->csr_lanes_per_row;
         if (tu && tu->csr_rows_per_cta > 0) rows = tu->csr_rows_per_cta;
-        if ((SW & (SW - 1)) != 0 || SW < 1 || SW > 32 || rows < 32 || rows > 1024 || rows % 32 != 0)
+        if ((SW & (SW - 1)) != 0 || SW < 1 || SW > 32 || rows < 1 || rows > 256)
             return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: bad CSR launch shape"));
+        e = prepare_csr_step();
+        if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: CSR setup: %s", cudaGetErrorString(e)));
         s->csr_SW = SW;
         s->csr_rows = rows;
+        const ion_status st3 = ion_setup_csr_staging(s, tu ? tu->csr_staging : 0);
+        if (st3 != ION_OK) return fail(st3);
     }
     if ((s->flags & ION_FLAG_SPLIT) && s->kind != ION_NO_GJ) {
         s->lps = 2;
@@ -419,7 +467,8 @@ static ion_status install_pulses(ion_sim *s, const ion_input *in) {
         ION_CK(s, cudaMemcpy(amp.data(), in->pulse_amp, np * sizeof(float), k));
     }
     for (int32_t p = 0; p < np; ++p) {
-        if (cell[p] < 0 || cell[p] >= s->n) return ion_fail(s, ION_ERR_INVALID_ARG, "pulse %d: cell %d out of range", p, cell[p]);
+        if (cell[p] < 0 || cell[p] >= s->n_user) return ion_fail(s, ION_ERR_INVALID_ARG, "pulse %d: cell %d out of range", p, cell[p]);
+        if (s->d_map) cell[p] = ion_batch_map_cell(s, cell[p]);   // user numbering -> padded segments
         if (end[p] < beg[p]) return ion_fail(s, ION_ERR_INVALID_ARG, "pulse %d: end before begin", p);
         if (!std::isfinite(amp[p])) return ion_fail(s, ION_ERR_INVALID_ARG, "pulse %d: amplitude not finite", p);
     }
@@ -529,7 +578,10 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
         a.fuse = split ? 0 : 1;
         a.ic_out = s->d_ic;
         a.vd_in = nullptr;
-        e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);
+        if (s->csr_staged && !split)
+            e = launch_csr_chunk_step(a, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, false, s->st);
+        else
+            e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);
         s->launches++;
         if (e == cudaSuccess && split) {
             CellArgs ca{c, s->d_ic};
@@ -668,6 +720,7 @@ float *ion_field_ptr(ion_sim *s, int32_t field) {
 
 extern "C" ion_status ion_state_device_ptr(ion_sim *s, int32_t field, float **out) {
     if (!s || !out || field < 0 || field >= NF) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_state_device_ptr: bad arguments");
+    if (s->d_map) return ion_fail(s, ION_ERR_UNSUPPORTED, "ion_state_device_ptr: not available for batches");
     if (s->state_sync_hook) {
         ion_status st = s->state_sync_hook(s);
         if (st != ION_OK) return st;
@@ -680,7 +733,7 @@ extern "C" ion_status ion_read_state(ion_sim *s, int32_t field, float *out, int6
     if (!s || !out) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_state: NULL argument");
     if (field != ION_FIELD_ALL && (field < 0 || field >= NF))
         return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_state: field %d out of range", field);
-    const int64_t need = field == ION_FIELD_ALL ? (int64_t)NF * s->n : s->n;
+    const int64_t need = field == ION_FIELD_ALL ? (int64_t)NF * s->n_user : s->n_user;
     if (count != need) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_state: count %lld, expected %lld", (long long)count, (long long)need);
     if (s->state_sync_hook) {
         ion_status st = s->state_sync_hook(s);
@@ -688,6 +741,10 @@ extern "C" ion_status ion_read_state(ion_sim *s, int32_t field, float *out, int6
     }
     const ion_status st = ion_sync(s);
     if (st != ION_OK && st != ION_ERR_NONFINITE && st != ION_ERR_TIMEOUT) return st;
+    if (s->d_map) {
+        const ion_status st2 = ion_batch_read(s, field, out);
+        return st2 != ION_OK ? st2 : st;
+    }
     if (field == ION_FIELD_ALL) {
         ION_CK(s, cudaMemcpy2D(out, s->n * sizeof(float), s->d_state, s->stride * sizeof(float), s->n * sizeof(float), NF,
                                cudaMemcpyDeviceToHost));
@@ -702,11 +759,15 @@ extern "C" ion_status ion_write_state(ion_sim *s, int32_t field, const float *in
     if (!s || !in) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_write_state: NULL argument");
     if (field != ION_FIELD_ALL && (field < 0 || field >= NF))
         return ion_fail(s, ION_ERR_INVALID_ARG, "ion_write_state: field %d out of range", field);
-    const int64_t need = field == ION_FIELD_ALL ? (int64_t)NF * s->n : s->n;
+    const int64_t need = field == ION_FIELD_ALL ? (int64_t)NF * s->n_user : s->n_user;
     if (count != need) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_write_state: count %lld, expected %lld", (long long)count, (long long)need);
     if (s->state_sync_hook) {
         ion_status st = s->state_sync_hook(s);
         if (st != ION_OK) return st;
+    }
+    if (s->d_map) {
+        ION_CK(s, cudaStreamSynchronize(s->st));
+        return ion_batch_write(s, field, in);
     }
     if (field == ION_FIELD_ALL) {
         ION_CK(s, cudaMemcpy2DAsync(s->d_state, s->stride * sizeof(float), in, s->n * sizeof(float), s->n * sizeof(float), NF,
@@ -774,9 +835,15 @@ extern "C" ion_status ion_read_trace(ion_sim *s, float *out, int64_t max_samples
     const int64_t avail = produced - first;
     const int64_t take = std::min(avail, max_samples);
     if (take > 0 && !out) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_trace: NULL out");
+    std::vector<float> tmp(s->d_map ? (size_t)s->n : 0);
     for (int64_t k = 0; k < take; ++k) {
         const int64_t slot = (first + k) % s->trace_cap;
-        ION_CK(s, cudaMemcpy(out + k * s->n, s->d_trace + slot * s->n, s->n * sizeof(float), cudaMemcpyDeviceToHost));
+        if (!s->d_map) {
+            ION_CK(s, cudaMemcpy(out + k * s->n, s->d_trace + slot * s->n, s->n * sizeof(float), cudaMemcpyDeviceToHost));
+        } else {   // batch: compact the padded sample into the user numbering
+            ION_CK(s, cudaMemcpy(tmp.data(), s->d_trace + slot * s->n, s->n * sizeof(float), cudaMemcpyDeviceToHost));
+            for (int64_t j = 0; j < s->n_user; ++j) out[k * s->n_user + j] = tmp[(size_t)ion_batch_map_cell(s, j)];
+        }
     }
     s->trace_read = first + take;
     *n_written = take;

@@ -1,0 +1,635 @@
+// ion_batch.cu -- many independent networks advanced by one launch per time step.
+//
+// Parameter sweeps run many small networks of uneven sizes and densities.  Each network
+// b gets a segment of the state arrays starting at seg_b (a multiple of 256 cells, the
+// tail padded like a single network's V_dend), so dense networks can stage their V_dend
+// with one 16-byte aligned bulk copy and CSR networks use global column indices into the
+// same arrays.  The work of a step is a list of tiles (network, first row, rows): a
+// dense tile is 8 warps x R rows of one network against all of that network's columns
+// (the single-network pair loop, ion_dense_core.cuh), a CSR tile is up to 256 rows with
+// SW lanes per row (ion_csr_core.cuh); every tile then runs the explicit-Euler update
+// of its rows.  Tiles are ordered by decreasing cost so the hardware scheduler packs the
+// long ones first; the launches of K steps are captured into one CUDA graph and
+// replayed.  ion_autotune times the tile shapes and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "ion.h"
+#include "ion_csr_core.cuh"
+#include "ion_dense_core.cuh"
+#include "ion_kernels.cuh"
+#include "ion_sim.h"
+
+namespace ion {
+
+enum TileKind : int32_t { TILE_DENSE = 0, TILE_CSR = 1 };
+
+struct BatchTile {
+    int32_t kind;
+    int32_t seg;     // first cell of the network's segment
+    int32_t n;       // cells of the network
+    int32_t n_pad;   // padded length of the segment (multiple of 256)
+    int32_t row0;    // first row (global cell index) of the tile
+    int32_t rows;    // rows of the tile
+    int32_t sw;      // CSR: lanes per row
+    float g;         // dense: pair weight
+};
+
+struct BatchArgs {
+    StepCommon c;    // c.n = padded total, c.S = state over the padded index space
+    const BatchTile *tiles;
+    const int32_t *row_ptr;   // padded-index CSR of every CSR network (other rows empty)
+    const int32_t *col;
+    const float *w;
+    int32_t kahan;
+};
+
+template <int SW>
+__device__ __forceinline__ void batch_csr_rows(const BatchArgs &a, const BatchTile &T, const float *vcur, float *ic_s) {
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    const int iters = (T.rows + nsub - 1) / nsub;
+    const bool vec = ((uintptr_t)a.col % 16 == 0) && ((uintptr_t)a.w % 16 == 0);
+    for (int it = 0; it < iters; ++it) {
+        const int rr = sub + it * nsub;
+        float acc = 0.0f;
+        if (rr < T.rows) {
+            const int i = T.row0 + rr;
+            const int e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
+            acc = vec ? csr_row_sum<SW, true, true>(vcur, a.col, a.w, e0, e1, vcur[i], li)
+                      : csr_row_sum<SW, false, true>(vcur, a.col, a.w, e0, e1, vcur[i], li);
+        }
+#pragma unroll
+        for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (li == 0 && rr < T.rows) ic_s[rr] = acc * (1.0f / GJ_SCALE);
+    }
+}
+
+// 256 threads: 8 warps.  Dense tiles: 8 row groups of R rows, one column split.
+template <int R>
+__global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ float red_s[32], red_c[32];
+    __shared__ float U_sh;
+    __shared__ float ic_s[256];
+
+    const BatchTile T = a.tiles[blockIdx.x];
+    const StepCommon &c = a.c;
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    float *vnext = vd_next(c, t);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (T.kind == TILE_DENSE) {
+        const DenseSmem sm = dense_smem(smem_raw, T.n_pad);   // one tile: n_pad <= 8192
+        const float *net_v = vcur + T.seg;
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            mbar_init(&bar[1], 1);
+            fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) issue_tile(sm, net_v, T.n_pad, 0, bar);
+        const float m_shift = net_v[0];
+        float ui[R];
+        const int local0 = T.row0 - T.seg;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int li = local0 + warp * R + r;
+            ui[r] = (warp * R + r < T.rows) ? (net_v[li] - m_shift) * GJ_SCALE : 0.0f;
+        }
+        uint32_t uses[2] = {0u, 0u};
+        float tot[R], Us, Uc;
+        if (!gj_pass<R, 1>(sm, net_v, T.n, T.n_pad, bar, uses, m_shift, ui, 0, lane, a.kahan, tot, Us, Uc)) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+                (void)mbar_wait_bounded(&bar[0], uses[0] & 1u);
+            }
+            return;
+        }
+        const float U = gj_reduce<R, 1>(sm, tot, Us, Uc, warp, 0, lane, red_s, red_c, &U_sh);
+        if ((int)threadIdx.x < T.rows) {
+            const int rr = threadIdx.x;
+            ic_s[rr] = row_current<1>(sm, rr, (net_v[local0 + rr] - m_shift) * GJ_SCALE, T.n, U, T.g);
+        }
+    } else {
+        switch (T.sw) {
+            case 1: batch_csr_rows<1>(a, T, vcur, ic_s); break;
+            case 2: batch_csr_rows<2>(a, T, vcur, ic_s); break;
+            case 4: batch_csr_rows<4>(a, T, vcur, ic_s); break;
+            case 8: batch_csr_rows<8>(a, T, vcur, ic_s); break;
+            case 16: batch_csr_rows<16>(a, T, vcur, ic_s); break;
+            default: batch_csr_rows<32>(a, T, vcur, ic_s); break;
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= T.rows) return;
+    const int64_t i = T.row0 + threadIdx.x;
+    const Cell cell = load_cell(c.S, vcur, i);
+    float iapp = pulse_current(c.pulses, i, t);
+    if (c.iapp != nullptr) iapp += c.iapp[i];
+    const CellNext o = cell_step(c.P, cell, ic_s[threadIdx.x], iapp);
+    finish_cell(c, t, vnext, i, o);
+}
+
+// gather / scatter between the user's numbering (consecutive cells) and the segments
+__global__ void batch_gather_kernel(const float *state, int64_t stride, const int32_t *map, int64_t n_user,
+                                    int32_t vd_slot_field, float *out) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_user) return;
+    const int64_t src = map[j];
+    for (int f = 0; f < NF; ++f) {
+        const int slot = (f == 0) ? vd_slot_field : f;
+        out[(int64_t)f * n_user + j] = state[(int64_t)slot * stride + src];
+    }
+}
+__global__ void batch_scatter_kernel(float *state, int64_t stride, const int32_t *map, int64_t n_user,
+                                     int32_t vd_slot_field, const float *in) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_user) return;
+    const int64_t dst = map[j];
+    for (int f = 0; f < NF; ++f) {
+        const int slot = (f == 0) ? vd_slot_field : f;
+        state[(int64_t)slot * stride + dst] = in[(int64_t)f * n_user + j];
+    }
+}
+
+}  // namespace ion
+
+using namespace ion;
+
+// ---- host side -------------------------------------------------------------------------
+struct BatchNet {
+    int32_t kind, n, n_pad, seg;
+    float g;
+    int64_t e0, nnz;  // CSR edges in the global arrays
+    int sw;
+};
+
+struct BatchExt {
+    std::vector<BatchNet> nets;
+    std::vector<int32_t> h_map;     // user cell -> padded cell
+    BatchTile *d_tiles = nullptr;
+    int n_tiles = 0;
+    int R = 2;                      // dense rows per warp (rows per dense tile = 8 R)
+    int csr_rows = 128;             // rows per CSR tile
+    int sw_scale = 0;               // 0: lanes per row from the degree; +-1: twice / half that
+    int max_dense_pad = 256;
+    float *d_tmp = nullptr;         // 19 x n_user staging for state I/O
+};
+
+static BatchExt *ext_of(ion_sim *s) { return static_cast<BatchExt *>(s->ext); }
+
+static int csr_sw_for(double deg, int scale) {
+    int sw, rows;
+    ion_choose_csr_shape(deg, &sw, &rows);
+    if (scale > 0 && sw < 32) sw *= 2;
+    if (scale < 0 && sw > 1) sw /= 2;
+    return sw;
+}
+
+// Build (or rebuild) the tile list for the current shape parameters.
+static ion_status batch_plan(ion_sim *s) {
+    BatchExt *X = ext_of(s);
+    std::vector<BatchTile> tiles;
+    std::vector<double> cost;
+    const int drows = 8 * X->R;
+    for (const BatchNet &b : X->nets) {
+        if (b.kind == ION_DENSE_UNIFORM) {
+            for (int r = 0; r < b.n; r += drows) {
+                BatchTile T{TILE_DENSE, b.seg, b.n, b.n_pad, b.seg + r, std::min(drows, b.n - r), 0, b.g};
+                tiles.push_back(T);
+                cost.push_back((double)T.rows * b.n_pad);
+            }
+        } else {
+            const double deg = b.n > 0 ? (double)b.nnz / b.n : 0.0;
+            for (int r = 0; r < b.n; r += X->csr_rows) {
+                BatchTile T{TILE_CSR, b.seg, b.n, b.n_pad, b.seg + r, std::min(X->csr_rows, b.n - r),
+                            csr_sw_for(deg, X->sw_scale), 0.0f};
+                tiles.push_back(T);
+                cost.push_back(3.0 * T.rows * deg + 60.0 * T.rows);
+            }
+        }
+    }
+    std::vector<int> order(tiles.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<BatchTile> sorted(tiles.size());
+    for (size_t k = 0; k < order.size(); ++k) sorted[k] = tiles[order[k]];
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess && X->d_tiles) e = cudaFree(X->d_tiles);
+    X->d_tiles = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&X->d_tiles, std::max<size_t>(1, sorted.size()) * sizeof(BatchTile));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(X->d_tiles, sorted.data(), sorted.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "batch plan: %s", cudaGetErrorString(e));
+    X->n_tiles = (int)sorted.size();
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    return ION_OK;
+}
+
+static size_t batch_smem(const BatchExt *X) { return (size_t)X->max_dense_pad * 4 + 8 * X->R * 4; }
+
+template <int R>
+static cudaError_t batch_launch_R(const BatchArgs &a, int tiles, size_t smem, cudaStream_t st, bool prepare) {
+    if (prepare)
+        return cudaFuncSetAttribute(batch_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    batch_step_kernel<R><<<tiles, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+static cudaError_t batch_launch(const BatchArgs &a, int R, int tiles, size_t smem, cudaStream_t st, bool prepare) {
+    switch (R) {
+        case 1: return batch_launch_R<1>(a, tiles, smem, st, prepare);
+        case 2: return batch_launch_R<2>(a, tiles, smem, st, prepare);
+        case 4: return batch_launch_R<4>(a, tiles, smem, st, prepare);
+        case 8: return batch_launch_R<8>(a, tiles, smem, st, prepare);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static cudaError_t batch_step(ion_sim *s, int k_off, const float *iapp) {
+    BatchExt *X = ext_of(s);
+    BatchArgs a{};
+    a.c = ion_step_common(s, k_off, iapp);
+    a.tiles = X->d_tiles;
+    a.row_ptr = s->d_rowptr;
+    a.col = s->d_col;
+    a.w = s->d_w;
+    a.kahan = 1;
+    s->launches++;
+    if (X->n_tiles == 0) return cudaSuccess;
+    return batch_launch(a, X->R, X->n_tiles, batch_smem(X), s->st, false);
+}
+
+static ion_status batch_prepare(ion_sim *s) {
+    BatchExt *X = ext_of(s);
+    cudaError_t e = batch_launch(BatchArgs{}, X->R, 0, batch_smem(X), s->st, true);
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "batch setup: %s", cudaGetErrorString(e));
+    return ION_OK;
+}
+
+// state I/O in the user's numbering
+ion_status ion_batch_read(ion_sim *s, int32_t field, float *out) {
+    BatchExt *X = ext_of(s);
+    const int64_t nu = (int64_t)X->h_map.size();
+    const int vd = (s->t & 1) ? 19 : 0;
+    batch_gather_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s->st>>>(s->d_state, s->stride, s->d_map, nu, vd,
+                                                                        X->d_tmp);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess) {
+        if (field == ION_FIELD_ALL)
+            e = cudaMemcpy(out, X->d_tmp, (size_t)NF * nu * sizeof(float), cudaMemcpyDeviceToHost);
+        else
+            e = cudaMemcpy(out, X->d_tmp + (int64_t)field * nu, (size_t)nu * sizeof(float), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "batch read: %s", cudaGetErrorString(e));
+    return ION_OK;
+}
+
+ion_status ion_batch_write(ion_sim *s, int32_t field, const float *in) {
+    BatchExt *X = ext_of(s);
+    const int64_t nu = (int64_t)X->h_map.size();
+    const int vd = (s->t & 1) ? 19 : 0;
+    cudaError_t e = cudaSuccess;
+    if (field != ION_FIELD_ALL) {   // read-modify-write of the one field through the staging buffer
+        batch_gather_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s->st>>>(s->d_state, s->stride, s->d_map, nu, vd,
+                                                                            X->d_tmp);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(X->d_tmp + (int64_t)field * nu, in, (size_t)nu * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(X->d_tmp, in, (size_t)NF * nu * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+        batch_scatter_kernel<<<(unsigned)((nu + 255) / 256), 256, 0, s->st>>>(s->d_state, s->stride, s->d_map, nu, vd,
+                                                                             X->d_tmp);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "batch write: %s", cudaGetErrorString(e));
+    return ION_OK;
+}
+
+int32_t ion_batch_map_cell(ion_sim *s, int64_t user_cell) {
+    BatchExt *X = ext_of(s);
+    if (user_cell < 0 || user_cell >= (int64_t)X->h_map.size()) return -1;
+    return X->h_map[(size_t)user_cell];
+}
+
+static void batch_free(ion_sim *s) {
+    BatchExt *X = ext_of(s);
+    if (!X) return;
+    cudaFree(X->d_tiles);
+    cudaFree(X->d_tmp);
+    cudaFree(s->d_map);
+    s->d_map = nullptr;
+    delete X;
+    s->ext = nullptr;
+}
+
+extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, const ion_conn *conns,
+                                       const ion_params *params, const float *init_state, ion_sim **out) {
+    if (!out) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: NULL out");
+    *out = nullptr;
+    if (n_nets < 1 || !nets || !conns || !params)
+        return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad arguments");
+    if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_PERSISTENT | ION_FLAG_SPLIT))
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: flags not supported for batches");
+    // validate and lay out
+    std::vector<BatchNet> bn((size_t)n_nets);
+    int64_t seg = 0, n_user = 0, nnz_total = 0;
+    int max_pad = 256;
+    for (int b = 0; b < n_nets; ++b) {
+        const ion_net &N = nets[b];
+        if (N.n_cells < 1 || (N.kind != ION_DENSE_UNIFORM && N.kind != ION_CSR && N.kind != ION_NO_GJ))
+            return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: network %d: bad size or kind", b);
+        if (N.kind == ION_DENSE_UNIFORM && N.n_cells > TJ)
+            return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: dense network %d has %d > %d cells", b,
+                            N.n_cells, TJ);
+        if (N.kind == ION_DENSE_UNIFORM && !std::isfinite(conns[b].g_c))
+            return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: network %d: g_c not finite", b);
+        if (N.kind == ION_CSR) {
+            if (conns[b].mem != ION_HOST)
+                return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: network %d: CSR must be host memory", b);
+            ion_status st = ion_validate_csr(N.n_cells, &conns[b]);
+            if (st != ION_OK) return st;
+        }
+        BatchNet &x = bn[(size_t)b];
+        x.kind = N.kind;
+        x.n = N.n_cells;
+        x.n_pad = (N.n_cells + PAD_J - 1) / PAD_J * PAD_J;
+        x.seg = (int32_t)seg;
+        x.g = N.kind == ION_DENSE_UNIFORM ? conns[b].g_c : 0.0f;
+        x.e0 = nnz_total;
+        x.nnz = N.kind == ION_CSR ? conns[b].nnz : 0;
+        if (N.kind == ION_DENSE_UNIFORM) max_pad = std::max(max_pad, x.n_pad);
+        seg += x.n_pad;
+        n_user += x.n;
+        nnz_total += x.nnz;
+        if (seg >= (1 << 30) || nnz_total >= INT32_MAX)
+            return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: batch too large");
+    }
+    // create an empty single-network handle of the padded size, then turn it into a batch
+    ion_net whole{(int32_t)seg, ION_NO_GJ};
+    ion_params p = *params;
+    p.flags &= ~(uint32_t)ION_FLAG_PERSISTENT;
+    ion_sim *s = nullptr;
+    ion_status st = ion_create(&whole, nullptr, &p, nullptr, &s);
+    if (st != ION_OK) return st;
+    auto fail = [&](ion_status code) {
+        ion_destroy(s);
+        return code;
+    };
+    BatchExt *X = new BatchExt();
+    s->ext = X;
+    s->extra_free = batch_free;
+    X->nets = bn;
+    X->max_dense_pad = max_pad;
+    X->h_map.resize((size_t)n_user);
+    {
+        int64_t u = 0;
+        for (const BatchNet &x : bn)
+            for (int i = 0; i < x.n; ++i) X->h_map[(size_t)u++] = x.seg + i;
+    }
+    const ion_tune *tu = (const ion_tune *)params->tune;
+    if (tu && tu->dense_rows_per_warp > 0) X->R = tu->dense_rows_per_warp;
+    if (tu && tu->csr_rows_per_cta > 0) X->csr_rows = tu->csr_rows_per_cta;
+    if ((X->R != 1 && X->R != 2 && X->R != 4 && X->R != 8) || X->csr_rows < 1 || X->csr_rows > 256)
+        return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad tile shape override"));
+    // global CSR over the padded index space
+    std::vector<int32_t> rp((size_t)seg + 1, 0), col((size_t)std::max<int64_t>(nnz_total, 1));
+    std::vector<float> w((size_t)std::max<int64_t>(nnz_total, 1));
+    for (int b = 0; b < n_nets; ++b) {
+        const BatchNet &x = bn[(size_t)b];
+        if (x.kind != ION_CSR) continue;
+        const ion_conn &C = conns[b];
+        for (int i = 0; i < x.n; ++i) rp[(size_t)x.seg + i + 1] = C.row_ptr[i + 1] - C.row_ptr[i];
+        for (int64_t e = 0; e < x.nnz; ++e) {
+            col[(size_t)(x.e0 + e)] = x.seg + C.col_idx[e];
+            w[(size_t)(x.e0 + e)] = C.weight ? C.weight[e] : C.g_c;
+        }
+    }
+    for (size_t i = 0; i < (size_t)seg; ++i) rp[i + 1] += rp[i];
+    // the per-row counts above were placed in network order, so the prefix sum lines the
+    // edges up with x.e0 (segments are laid out in network order)
+    cudaError_t e = cudaMalloc(&s->d_rowptr, rp.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_col, col.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_w, w.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_map, X->h_map.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&X->d_tmp, (size_t)NF * n_user * sizeof(float));
+    if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create_batch: %s", cudaGetErrorString(e)));
+    s->own_csr = true;
+    s->nnz = nnz_total;
+    e = cudaMemcpy(s->d_rowptr, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_map, X->h_map.data(), X->h_map.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create_batch: %s", cudaGetErrorString(e)));
+    for (BatchNet &x : X->nets)
+        if (x.kind == ION_CSR) x.sw = csr_sw_for((double)x.nnz / x.n, 0);
+    s->kind = ION_CSR;   // the generic paths see a CSR handle; stepping is overridden
+    s->n_user = n_user;
+    s->step_override = batch_step;
+    s->prepare_hook = nullptr;
+    // every V_dend padding cell holds the sentinel (the default state wrote V_0 there)
+    for (const BatchNet &x : X->nets) {
+        if (x.n_pad > x.n) {
+            e = launch_fill(s->d_state + x.seg + x.n, PAD_VOLT, x.n_pad - x.n, s->st);
+            if (e == cudaSuccess) e = launch_fill(s->d_state + 19 * s->stride + x.seg + x.n, PAD_VOLT, x.n_pad - x.n, s->st);
+            if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create_batch: %s", cudaGetErrorString(e)));
+        }
+    }
+    if (init_state) {
+        st = ion_batch_write(s, ION_FIELD_ALL, init_state);
+        if (st != ION_OK) return fail(st);
+    }
+    st = batch_plan(s);
+    if (st == ION_OK) st = batch_prepare(s);
+    if (st != ION_OK) return fail(st);
+    *out = s;
+    return ION_OK;
+}
+
+// ---- autotuner ------------------------------------------------------------------------------
+// Times candidate launch shapes on the handle's own network(s), `steps` time steps each
+// (direct launches, CUDA events), and keeps the fastest.  The state and step count are
+// saved before and restored after, so tuning does not advance the simulation.
+static ion_status time_steps(ion_sim *s, int steps, float *ms) {
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int64_t t_save = s->t;
+    cudaEventRecord(a, s->st);
+    const uint32_t flags = s->flags;
+    s->flags |= ION_FLAG_NO_GRAPH;
+    ion_status st = ion_step(s, steps, nullptr);
+    s->flags = flags;
+    cudaEventRecord(b, s->st);
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    (void)t_save;
+    if (st != ION_OK) return st;
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(e));
+    return ION_OK;
+}
+
+extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) {
+    if (!s || steps < 1) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_autotune: bad arguments");
+    if (s->run_override) return ion_fail(s, ION_ERR_UNSUPPORTED, "ion_autotune: persistent handles are not tuned");
+    // save the state and the step counter
+    float *save = nullptr;
+    const size_t bytes = (size_t)20 * s->stride * sizeof(float);
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess) e = cudaMalloc(&save, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(save, s->d_state, bytes, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "ion_autotune: %s", cudaGetErrorString(e));
+    const int64_t t0 = s->t;
+    auto restore = [&]() {
+        cudaStreamSynchronize(s->st);
+        cudaMemcpy(s->d_state, save, bytes, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(s->d_t, &t0, sizeof t0, cudaMemcpyHostToDevice);
+        s->t = t0;
+    };
+    float best = 1e30f;
+    ion_tune bt{};
+    ion_status st = ION_OK;
+    if (s->ext && s->step_override == batch_step) {
+        BatchExt *X = ext_of(s);
+        const int Rs[] = {1, 2, 4, 8};
+        const int rows[] = {64, 128, 256};
+        const int scales[] = {0, 1, -1};
+        int bR = X->R, brows = X->csr_rows, bsc = X->sw_scale;
+        for (int R : Rs)
+            for (int r : rows)
+                for (int sc : scales) {
+                    X->R = R;
+                    X->csr_rows = r;
+                    X->sw_scale = sc;
+                    st = batch_plan(s);
+                    if (st == ION_OK) st = batch_prepare(s);
+                    float ms = 0;
+                    if (st == ION_OK) st = time_steps(s, steps, &ms);
+                    restore();
+                    if (st != ION_OK) break;
+                    if (ms < best) {
+                        best = ms;
+                        bR = R;
+                        brows = r;
+                        bsc = sc;
+                    }
+                }
+        X->R = bR;
+        X->csr_rows = brows;
+        X->sw_scale = bsc;
+        if (st == ION_OK) st = batch_plan(s);
+        if (st == ION_OK) st = batch_prepare(s);
+        bt.dense_rows_per_warp = bR;
+        bt.dense_warps = 8;
+        bt.dense_col_splits = 1;
+        bt.csr_rows_per_cta = brows;
+        bt.csr_lanes_per_row = bsc;   // scale of the degree-based choice: 0, +1 (x2), -1 (/2)
+    } else if (s->kind == ION_DENSE_UNIFORM) {
+        int R0, W0, G0;
+        ion_choose_dense_shape(s->n, s->sms, &R0, &W0, &G0);
+        struct Shape { int R, W, GJ; };
+        std::vector<Shape> cand = {{R0, W0, G0}};
+        const int Rs[] = {1, 2, 4, 6, 8};
+        const int GJs[] = {1, 2, 4};
+        for (int R : Rs)
+            for (int GJ : GJs)
+                for (int GR = 1; GR <= 32; ++GR) {
+                    const int W = GR * GJ;
+                    if (W * 32 > dense_max_threads(R) || W < 8) continue;
+                    const long rows_cta = (long)GR * R;
+                    const long grid = (s->n + rows_cta - 1) / rows_cta;
+                    const long cost = ((grid + s->sms - 1) / s->sms) * (rows_cta + 4);
+                    const long grid0 = (s->n + (long)(W0 / G0) * R0 - 1) / ((long)(W0 / G0) * R0);
+                    const long cost0 = ((grid0 + s->sms - 1) / s->sms) * ((long)(W0 / G0) * R0 + 4);
+                    if (cost <= cost0 * 11 / 10 && cand.size() < 12 && !(R == R0 && W == W0 && GJ == G0))
+                        cand.push_back({R, W, GJ});
+                }
+        Shape bs = cand[0];
+        for (const Shape &c : cand) {
+            if (prepare_dense_step(c.R, c.W, c.GJ, s->n_pad) != cudaSuccess) continue;
+            s->dense_R = c.R;
+            s->dense_W = c.W;
+            s->dense_GJ = c.GJ;
+            float ms = 0;
+            st = time_steps(s, steps, &ms);
+            restore();
+            if (st != ION_OK) break;
+            if (ms < best) {
+                best = ms;
+                bs = c;
+            }
+        }
+        s->dense_R = bs.R;
+        s->dense_W = bs.W;
+        s->dense_GJ = bs.GJ;
+        prepare_dense_step(bs.R, bs.W, bs.GJ, s->n_pad);
+        bt.dense_rows_per_warp = bs.R;
+        bt.dense_warps = bs.W;
+        bt.dense_col_splits = bs.GJ;
+    } else if (s->kind == ION_CSR) {
+        const int SWs[] = {1, 2, 4, 8, 16, 32};
+        const int rows[] = {32, 64, 128, 256};
+        int bsw = s->csr_SW, brows = s->csr_rows, bstaged = s->csr_staged;
+        int b_csw = s->csr_chunk_SW;
+        const int sw0 = s->csr_SW;
+        for (int staged = 0; staged <= 1 && st == ION_OK; ++staged) {
+            if (staged && ion_setup_csr_staging(s, 2) != ION_OK) break;
+            s->csr_staged = staged;
+            for (int sw : SWs) {
+                if (sw * 4 < sw0 || sw > sw0 * 4) continue;   // near the degree-based choice
+                for (int r : rows) {
+                    if (staged && r != rows[0]) continue;     // staged: rows per CTA fixed by the SM count
+                    if (staged) s->csr_chunk_SW = sw;
+                    else {
+                        s->csr_SW = sw;
+                        s->csr_rows = r;
+                    }
+                    float ms = 0;
+                    st = time_steps(s, steps, &ms);
+                    restore();
+                    if (st != ION_OK) break;
+                    if (ms < best) {
+                        best = ms;
+                        bstaged = staged;
+                        if (staged) b_csw = sw;
+                        else {
+                            bsw = sw;
+                            brows = r;
+                        }
+                    }
+                }
+            }
+        }
+        s->csr_SW = bsw;
+        s->csr_rows = brows;
+        s->csr_staged = bstaged;
+        s->csr_chunk_SW = b_csw;
+        bt.csr_lanes_per_row = bstaged ? b_csw : bsw;
+        bt.csr_rows_per_cta = bstaged ? s->csr_chunk_rows : brows;
+        bt.csr_staging = bstaged ? 2 : 1;
+    }
+    if (s->gexec) {
+        cudaGraphExecDestroy(s->gexec);
+        s->gexec = nullptr;
+    }
+    cudaFree(save);
+    if (st != ION_OK) return st;
+    if (chosen) *chosen = bt;
+    return ION_OK;
+}

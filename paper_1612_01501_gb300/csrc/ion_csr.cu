@@ -3,74 +3,46 @@
 // Algorithm 1 over a programmed weight matrix (Sec. 2.3): for every stored connection
 // e = (i, j) of row i,
 //   Ic_i += w_e (0.8 e^{-dV^2/100} + 0.2) dV,  dV = V_dend,i - V_dend,j.
-// One CTA owns `rows_per_cta` consecutive rows (= its thread count).  Phase 1: groups of
-// SW lanes (SW = 1..32, picked from the mean degree) walk one row's edges with a stride
-// of SW, so the index and weight loads of a group are contiguous; four edges per lane
-// are in flight per iteration to hide the latency of the V_dend gathers; the SW lane
-// sums are combined with shuffles in a fixed order.  Phase 2: one thread per row runs
-// the explicit-Euler cell update with that row's current (fused variant), so the cell
-// work runs on full warps whatever SW is.
+// A CTA of 256 threads owns `rows` consecutive rows (1..256, chosen from the mean degree
+// so that the grid keeps every SM busy).  Phase 1: groups of SW lanes (SW = 1..32) walk
+// one row's edges; with 16-byte aligned arrays each lane reads four consecutive indices
+// and weights per 16-byte load, and four V_dend gathers are in flight per lane; the SW
+// lane sums are combined with shuffles in a fixed order.  Phase 2: one thread per row
+// runs the explicit-Euler cell update with that row's current (fused variant), so the
+// cell work runs on full warps whatever SW is.
 #include <cuda_runtime.h>
 
+#include "ion_async.cuh"
+#include "ion_csr_core.cuh"
 #include "ion_kernels.cuh"
 
 namespace ion {
 
-__device__ __forceinline__ float gj_edge(float vi, float vj, float w) {
-    const float du = (vi - vj) * GJ_SCALE;
-    return w * fmaf(0.8f, ex2_approx(-du * du), 0.2f) * du;
-}
-
-template <int SW>
-__global__ void __launch_bounds__(1024) csr_step_kernel(const CsrArgs a) {
-    extern __shared__ float ic_s[];
+// One CTA of 256 threads owns `rows` consecutive rows (rows <= 256).  Phase 1: groups of
+// SW lanes take the rows round-robin; phase 2: thread t updates row t.
+template <int SW, bool VEC, bool HAS_W>
+__global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows) {
+    __shared__ float ic_s[256];
     const StepCommon &c = a.c;
     const int n = c.n;
-    const int rows_cta = blockDim.x;
-    const int row0 = blockIdx.x * rows_cta;
+    const int row0 = blockIdx.x * rows;
     const int64_t t = step_index(c);
     const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
     float *vnext = a.fuse ? vd_next(c, t) : nullptr;
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
-    const float *__restrict__ w = a.w;
-    const int32_t *__restrict__ col = a.col;
-
-    for (int rr = sub; rr < rows_cta; rr += nsub) {   // SW iterations for every lane
+    const int iters = (rows + nsub - 1) / nsub;          // the same for every lane (shuffles below)
+    for (int it = 0; it < iters; ++it) {
+        const int rr = sub + it * nsub;
         const int i = row0 + rr;
         float acc = 0.0f;
-        if (i < n) {
-            const float vi = vcur[i];
-            const int e1 = a.row_ptr[i + 1];
-            int e = a.row_ptr[i] + li;
-            if (w != nullptr) {
-                for (; e + 3 * SW < e1; e += 4 * SW) {
-                    const int j0 = __ldg(col + e), j1 = __ldg(col + e + SW), j2 = __ldg(col + e + 2 * SW),
-                              j3 = __ldg(col + e + 3 * SW);
-                    const float w0 = __ldg(w + e), w1 = __ldg(w + e + SW), w2 = __ldg(w + e + 2 * SW),
-                                w3 = __ldg(w + e + 3 * SW);
-                    const float v0 = __ldg(vcur + j0), v1 = __ldg(vcur + j1), v2 = __ldg(vcur + j2),
-                                v3 = __ldg(vcur + j3);
-                    acc += gj_edge(vi, v0, w0) + gj_edge(vi, v1, w1) + (gj_edge(vi, v2, w2) + gj_edge(vi, v3, w3));
-                }
-                for (; e < e1; e += SW) acc += gj_edge(vi, __ldg(vcur + __ldg(col + e)), __ldg(w + e));
-            } else {
-                for (; e + 3 * SW < e1; e += 4 * SW) {
-                    const int j0 = __ldg(col + e), j1 = __ldg(col + e + SW), j2 = __ldg(col + e + 2 * SW),
-                              j3 = __ldg(col + e + 3 * SW);
-                    const float v0 = __ldg(vcur + j0), v1 = __ldg(vcur + j1), v2 = __ldg(vcur + j2),
-                                v3 = __ldg(vcur + j3);
-                    acc += gj_edge(vi, v0, 1.0f) + gj_edge(vi, v1, 1.0f) +
-                           (gj_edge(vi, v2, 1.0f) + gj_edge(vi, v3, 1.0f));
-                }
-                for (; e < e1; e += SW) acc += gj_edge(vi, __ldg(vcur + __ldg(col + e)), 1.0f);
-                acc *= a.g;
-            }
-        }
+        if (rr < rows && i < n)
+            acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li);
 #pragma unroll
         for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (li == 0 && i < n) ic_s[rr] = acc * (1.0f / GJ_SCALE);
+        if (li == 0 && rr < rows) ic_s[rr] = (HAS_W ? acc : acc * a.g) * (1.0f / GJ_SCALE);
     }
     __syncthreads();
+    if ((int)threadIdx.x >= rows) return;
     const int i = row0 + threadIdx.x;
     if (i >= n) return;
     const float ic = ic_s[threadIdx.x];
@@ -85,15 +57,22 @@ __global__ void __launch_bounds__(1024) csr_step_kernel(const CsrArgs a) {
     finish_cell(c, t, vnext, i, o);
 }
 
-template <int SW>
-static cudaError_t launch_csr_SW(const CsrArgs &a, int rows, cudaStream_t st) {
+template <int SW, bool VEC, bool HAS_W>
+static cudaError_t launch_csr_T(const CsrArgs &a, int rows, cudaStream_t st) {
     const int grid = (a.c.n + rows - 1) / rows;
-    csr_step_kernel<SW><<<grid, rows, rows * sizeof(float), st>>>(a);
+    csr_step_kernel<SW, VEC, HAS_W><<<grid, 256, 0, st>>>(a, rows);
     return cudaGetLastError();
 }
+template <int SW>
+static cudaError_t launch_csr_SW(const CsrArgs &a, int rows, cudaStream_t st) {
+    const bool vec = ((uintptr_t)a.col % 16 == 0) && (a.w == nullptr || (uintptr_t)a.w % 16 == 0);
+    if (a.w != nullptr) return vec ? launch_csr_T<SW, true, true>(a, rows, st) : launch_csr_T<SW, false, true>(a, rows, st);
+    return vec ? launch_csr_T<SW, true, false>(a, rows, st) : launch_csr_T<SW, false, false>(a, rows, st);
+}
 
+// rows: rows per CTA (1..256); SW: lanes per row.
 cudaError_t launch_csr_step(const CsrArgs &a, int SW, int rows, cudaStream_t st) {
-    if (rows < 32 || rows > 1024 || rows % 32 != 0) return cudaErrorInvalidValue;
+    if (rows < 1 || rows > 256) return cudaErrorInvalidValue;
     switch (SW) {
         case 1: return launch_csr_SW<1>(a, rows, st);
         case 2: return launch_csr_SW<2>(a, rows, st);
@@ -103,6 +82,170 @@ cudaError_t launch_csr_step(const CsrArgs &a, int SW, int rows, cudaStream_t st)
         case 32: return launch_csr_SW<32>(a, rows, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+// Prefer L1 over shared memory for the V_dend gathers (the kernel uses 1 KB of shared).
+template <int SW>
+static void carveout_SW() {
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+}
+cudaError_t prepare_csr_step() {
+    carveout_SW<1>();
+    carveout_SW<2>();
+    carveout_SW<4>();
+    carveout_SW<8>();
+    carveout_SW<16>();
+    carveout_SW<32>();
+    return cudaGetLastError();
+}
+
+// ---- column-chunked variant: V_dend staged in shared memory -------------------------------
+// For large networks the V_dend gathers of a random graph touch a different L1 line per
+// lane.  Here the column space is cut into chunks of CSR_CHUNK floats (128 KB); each
+// CTA (one per SM, 1024 threads) owns `rows` consecutive rows and, chunk by chunk,
+// stages V_dend[chunk] into shared memory with one bulk copy and sums the edges of its
+// rows whose columns fall in that chunk (the per-row chunk boundaries are precomputed:
+// mid[(c-1) * n + i] is the first edge of row i in chunk c).  The gathers then hit shared
+// memory while the indices and weights stream from HBM.
+template <int SW, bool VEC, bool HAS_W>
+__global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, int rows, const int32_t *mid,
+                                                              int n_chunks) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *vs = reinterpret_cast<float *>(smem_raw);
+    float *ic_s = vs + min(CSR_CHUNK, a.c.n_pad);
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int ok_sh;
+    const StepCommon &c = a.c;
+    const int n = c.n;
+    const int row0 = blockIdx.x * rows;
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    float *vnext = vd_next(c, t);
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    const int iters = (rows + nsub - 1) / nsub;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) ic_s[r] = 0.0f;
+    __syncthreads();
+    for (int ch = 0; ch < n_chunks; ++ch) {
+        const int c0 = ch * CSR_CHUNK;
+        const int len = min(CSR_CHUNK, c.n_pad - c0);
+        if (threadIdx.x == 0) {
+            mbar_expect_tx(&bar, (uint32_t)len * 4u);
+            bulk_g2s(vs, vcur + c0, (uint32_t)len * 4u, &bar);
+        }
+        const bool landed = mbar_wait_bounded(&bar, (uint32_t)(ch & 1));
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+                (void)mbar_wait_bounded(&bar, (uint32_t)(ch & 1));
+            }
+            return;
+        }
+        for (int it = 0; it < iters; ++it) {
+            const int rr = sub + it * nsub;
+            const int i = row0 + rr;
+            float acc = 0.0f;
+            if (rr < rows && i < n) {
+                const int e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
+                const int e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+                acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vcur[i], li);
+            }
+#pragma unroll
+            for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+            if (li == 0 && rr < rows) ic_s[rr] += acc;
+        }
+        // all reads of this chunk are done before the next bulk copy overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
+    for (int rr = threadIdx.x; rr < rows; rr += blockDim.x) {
+        const int i = row0 + rr;
+        if (i >= n) break;
+        const float ic = (HAS_W ? ic_s[rr] : ic_s[rr] * a.g) * (1.0f / GJ_SCALE);
+        const Cell cell = load_cell(c.S, vcur, i);
+        float iapp = pulse_current(c.pulses, i, t);
+        if (c.iapp != nullptr) iapp += c.iapp[i];
+        const CellNext o = cell_step(c.P, cell, ic, iapp);
+        finish_cell(c, t, vnext, i, o);
+    }
+}
+
+size_t csr_chunk_smem_bytes(int n_pad, int rows) {
+    return (size_t)(n_pad < CSR_CHUNK ? n_pad : CSR_CHUNK) * sizeof(float) + (size_t)rows * sizeof(float);
+}
+
+template <int SW, bool VEC, bool HAS_W>
+static cudaError_t chunk_T(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
+                           cudaStream_t st) {
+    const size_t smem = csr_chunk_smem_bytes(a.c.n_pad, rows);
+    if (prepare)
+        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem);
+    const int grid = (a.c.n + rows - 1) / rows;
+    csr_chunk_step_kernel<SW, VEC, HAS_W><<<grid, 1024, smem, st>>>(a, rows, mid, n_chunks);
+    return cudaGetLastError();
+}
+template <int SW>
+static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
+                            cudaStream_t st) {
+    const bool vec = ((uintptr_t)a.col % 16 == 0) && (a.w == nullptr || (uintptr_t)a.w % 16 == 0);
+    if (prepare) {   // set the limit on every instantiation the launch may pick
+        cudaError_t e = chunk_T<SW, true, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, false, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, false>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, false, false>(a, rows, mid, n_chunks, true, st);
+        return e;
+    }
+    if (a.w != nullptr)
+        return vec ? chunk_T<SW, true, true>(a, rows, mid, n_chunks, false, st)
+                   : chunk_T<SW, false, true>(a, rows, mid, n_chunks, false, st);
+    return vec ? chunk_T<SW, true, false>(a, rows, mid, n_chunks, false, st)
+               : chunk_T<SW, false, false>(a, rows, mid, n_chunks, false, st);
+}
+
+// rows: rows per CTA (1..1024); mid: (n_chunks - 1) x n interior chunk boundaries.
+cudaError_t launch_csr_chunk_step(const CsrArgs &a, int SW, int rows, const int32_t *mid, int n_chunks, bool prepare,
+                                  cudaStream_t st) {
+    if (rows < 1 || rows > 1024 || n_chunks < 1) return cudaErrorInvalidValue;
+    switch (SW) {
+        case 1: return chunk_SW<1>(a, rows, mid, n_chunks, prepare, st);
+        case 2: return chunk_SW<2>(a, rows, mid, n_chunks, prepare, st);
+        case 4: return chunk_SW<4>(a, rows, mid, n_chunks, prepare, st);
+        case 8: return chunk_SW<8>(a, rows, mid, n_chunks, prepare, st);
+        case 16: return chunk_SW<16>(a, rows, mid, n_chunks, prepare, st);
+        case 32: return chunk_SW<32>(a, rows, mid, n_chunks, prepare, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// mid[(c - 1) * n + i] = first edge of row i whose column is >= c * CSR_CHUNK (c = 1..C-1)
+__global__ void csr_chunk_bounds_kernel(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
+                                        int32_t *mid) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int ch = 1; ch < n_chunks; ++ch) {
+        const int bound = ch * CSR_CHUNK;
+        int lo = row_ptr[i], hi = row_ptr[i + 1];   // first e in [lo, hi) with col[e] >= bound
+        while (lo < hi) {
+            const int m = (lo + hi) >> 1;
+            if (col[m] < bound) lo = m + 1;
+            else hi = m;
+        }
+        mid[(int64_t)(ch - 1) * n + i] = lo;
+    }
+}
+
+cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks, int32_t *mid,
+                                    cudaStream_t st) {
+    if (n_chunks <= 1) return cudaSuccess;
+    csr_chunk_bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, col, n, n_chunks, mid);
+    return cudaGetLastError();
 }
 
 // ---- stand-alone cell update (no gap junctions, or Ic computed by another launch) ----

@@ -1,0 +1,73 @@
+// ion_csr_core.cuh -- the per-row CSR gap-junction sum shared by the single-network
+// kernel (ion_csr.cu) and the batched kernel (ion_batch.cu).
+#pragma once
+#include <cstdint>
+
+#include "ion_kernels.cuh"
+
+namespace ion {
+
+__device__ __forceinline__ float gj_edge(float vi, float vj, float w) {
+    const float du = (vi - vj) * GJ_SCALE;
+    return w * fmaf(0.8f, ex2_approx(-du * du), 0.2f) * du;
+}
+
+// Sum of one row's edges [e0, e1) handled by lane li of an SW-lane group.  VEC: the index
+// and weight arrays are 16-byte aligned, so the body of the row is read four edges per
+// lane with one 16-byte load each (a head of up to three edges and a tail are read one
+// by one).  Four V_dend gathers are in flight per lane per iteration.
+template <int SW, bool VEC, bool HAS_W>
+__device__ __forceinline__ float csr_row_sum(const float *__restrict__ vcur, const int32_t *__restrict__ col,
+                                             const float *__restrict__ w, int e0, int e1, float vi, int li) {
+    float acc = 0.0f;
+    if (VEC) {
+        const int ea = min(e1, (e0 + 3) & ~3);                 // first 16-byte aligned edge
+        const int eb = ea + ((e1 - ea) & ~3);                   // end of the aligned body
+        for (int e = e0 + li; e < ea; e += SW) acc += gj_edge(vi, __ldg(vcur + __ldg(col + e)), HAS_W ? __ldg(w + e) : 1.0f);
+        for (int e = ea + 4 * li; e < eb; e += 4 * SW) {
+            const int4 j = __ldg(reinterpret_cast<const int4 *>(col + e));
+            float4 ww = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+            if (HAS_W) ww = __ldg(reinterpret_cast<const float4 *>(w + e));
+            const float v0 = __ldg(vcur + j.x), v1 = __ldg(vcur + j.y), v2 = __ldg(vcur + j.z), v3 = __ldg(vcur + j.w);
+            acc += (gj_edge(vi, v0, ww.x) + gj_edge(vi, v1, ww.y)) + (gj_edge(vi, v2, ww.z) + gj_edge(vi, v3, ww.w));
+        }
+        for (int e = eb + li; e < e1; e += SW) acc += gj_edge(vi, __ldg(vcur + __ldg(col + e)), HAS_W ? __ldg(w + e) : 1.0f);
+    } else {
+        int e = e0 + li;
+        for (; e + 3 * SW < e1; e += 4 * SW) {
+            const int j0 = __ldg(col + e), j1 = __ldg(col + e + SW), j2 = __ldg(col + e + 2 * SW), j3 = __ldg(col + e + 3 * SW);
+            const float w0 = HAS_W ? __ldg(w + e) : 1.0f, w1 = HAS_W ? __ldg(w + e + SW) : 1.0f;
+            const float w2 = HAS_W ? __ldg(w + e + 2 * SW) : 1.0f, w3 = HAS_W ? __ldg(w + e + 3 * SW) : 1.0f;
+            const float v0 = __ldg(vcur + j0), v1 = __ldg(vcur + j1), v2 = __ldg(vcur + j2), v3 = __ldg(vcur + j3);
+            acc += (gj_edge(vi, v0, w0) + gj_edge(vi, v1, w1)) + (gj_edge(vi, v2, w2) + gj_edge(vi, v3, w3));
+        }
+        for (; e < e1; e += SW) acc += gj_edge(vi, __ldg(vcur + __ldg(col + e)), HAS_W ? __ldg(w + e) : 1.0f);
+    }
+    return acc;
+}
+
+// Sum of one row's edges [e0, e1) whose columns all lie in the shared-memory chunk that
+// starts at global column c0 (vs holds V_dend[c0 ...]).  Same lane layout as csr_row_sum.
+template <int SW, bool VEC, bool HAS_W>
+__device__ __forceinline__ float csr_row_sum_smem(const float *vs, int c0, const int32_t *__restrict__ col,
+                                                  const float *__restrict__ w, int e0, int e1, float vi, int li) {
+    float acc = 0.0f;
+    if (VEC) {
+        const int ea = min(e1, (e0 + 3) & ~3);
+        const int eb = ea + ((e1 - ea) & ~3);
+        for (int e = e0 + li; e < ea; e += SW) acc += gj_edge(vi, vs[__ldg(col + e) - c0], HAS_W ? __ldg(w + e) : 1.0f);
+        for (int e = ea + 4 * li; e < eb; e += 4 * SW) {
+            const int4 j = __ldcs(reinterpret_cast<const int4 *>(col + e));     // streamed once per step
+            float4 ww = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+            if (HAS_W) ww = __ldcs(reinterpret_cast<const float4 *>(w + e));
+            const float v0 = vs[j.x - c0], v1 = vs[j.y - c0], v2 = vs[j.z - c0], v3 = vs[j.w - c0];
+            acc += (gj_edge(vi, v0, ww.x) + gj_edge(vi, v1, ww.y)) + (gj_edge(vi, v2, ww.z) + gj_edge(vi, v3, ww.w));
+        }
+        for (int e = eb + li; e < e1; e += SW) acc += gj_edge(vi, vs[__ldg(col + e) - c0], HAS_W ? __ldg(w + e) : 1.0f);
+    } else {
+        for (int e = e0 + li; e < e1; e += SW) acc += gj_edge(vi, vs[__ldg(col + e) - c0], HAS_W ? __ldg(w + e) : 1.0f);
+    }
+    return acc;
+}
+
+}  // namespace ion

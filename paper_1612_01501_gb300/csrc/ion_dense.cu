@@ -24,152 +24,10 @@
 #include <cuda_runtime.h>
 
 #include "ion_async.cuh"
+#include "ion_dense_core.cuh"
 #include "ion_kernels.cuh"
 
 namespace ion {
-
-constexpr float PAD_U = 1.0e6f;   // |u| of padded columns: 2^{-PAD_U^2} is exactly 0
-
-struct DenseSmem {
-    float *tile0;     // buffer b at tile0 + b * buf_len
-    int buf_len;
-    int n_tiles;
-    float *part;      // [rows_cta][GJ] row sums per column split
-};
-
-__device__ __forceinline__ DenseSmem dense_smem(unsigned char *raw, int n_pad) {
-    DenseSmem s;
-    s.tile0 = reinterpret_cast<float *>(raw);
-    s.n_tiles = (n_pad + TJ - 1) / TJ;
-    s.buf_len = s.n_tiles > 1 ? TJ : n_pad;
-    s.part = s.tile0 + (s.n_tiles > 1 ? 2 * TJ : n_pad);
-    return s;
-}
-
-// Issue the bulk copy of tile k (thread 0 only).
-__device__ __forceinline__ void issue_tile(const DenseSmem &sm, const float *src, int n_pad, int k, uint64_t *bar) {
-    const int len = min(TJ, n_pad - k * TJ);
-    mbar_expect_tx(&bar[k & 1], (uint32_t)len * 4u);
-    bulk_g2s(sm.tile0 + (k & 1) * sm.buf_len, src + (int64_t)k * TJ, (uint32_t)len * 4u, &bar[k & 1]);
-}
-
-// One pass over all columns.  If `src` is non-NULL the first two tiles must already be in
-// flight (issue_tile) and the remaining ones are issued here; if NULL the single tile
-// already holds raw V_dend (single-CTA persistent mode).  On return tot[r] holds this
-// lane's compensated column sum for row r, and (Us, Uc) this thread's share of
-// sum_j u_j.  bar_uses counts completed phases of each mbarrier.  Returns false (in
-// every thread) if a bulk copy did not land in time.
-template <int R, int GJ>
-__device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, int n, int n_pad, uint64_t *bar,
-                                        uint32_t (&bar_uses)[2], float m_shift, const float (&ui)[R], int cs,
-                                        int lane, int kahan, float (&tot)[R], float &Us, float &Uc) {
-    float ks[R], kc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) ks[r] = kc[r] = 0.0f;
-    Us = Uc = 0.0f;
-    for (int kt = 0; kt < sm.n_tiles; ++kt) {
-        const int b = kt & 1;
-        const int j0 = kt * TJ;
-        const int len = min(TJ, n_pad - j0);
-        if (src != nullptr) {
-            const bool landed = mbar_wait_bounded(&bar[b], bar_uses[b] & 1u);
-            bar_uses[b]++;
-            if (__syncthreads_or(!landed)) return false;   // block-uniform decision
-        }
-        float *tb = sm.tile0 + b * sm.buf_len;
-        for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            const bool real = j0 + j < n;
-            const float u = (tb[j] - m_shift) * GJ_SCALE;
-            tb[j] = real ? -u : -PAD_U;
-            if (real) kahan_add(Us, Uc, u);
-        }
-        __syncthreads();
-        const float4 *t4 = reinterpret_cast<const float4 *>(tb);
-        const int n4 = len >> 2;             // float4 columns; len is a multiple of 256
-        constexpr int BLK = 16;              // float4 loads per lane between Kahan folds
-        for (int m0 = cs * 32 + lane; m0 < n4; m0 += 32 * GJ * BLK) {
-            float2 acc[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
-#pragma unroll 4
-            for (int mm = 0; mm < BLK; ++mm) {
-                const int m = m0 + mm * 32 * GJ;
-                if (m < n4) {
-                    const float4 v = t4[m];
-                    const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 u2 = make_float2(ui[r], ui[r]);
-                        const float2 da = __fadd2_rn(u2, va);
-                        const float2 db = __fadd2_rn(u2, vb);
-                        const float2 qa = __fmul2_rn(da, da);
-                        const float2 qb = __fmul2_rn(db, db);
-                        const float2 ea = make_float2(ex2_approx(-qa.x), ex2_approx(-qa.y));
-                        const float2 eb = make_float2(ex2_approx(-qb.x), ex2_approx(-qb.y));
-                        acc[r] = __ffma2_rn(ea, da, acc[r]);
-                        acc[r] = __ffma2_rn(eb, db, acc[r]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const float blk = acc[r].x + acc[r].y;
-                if (kahan) kahan_add(ks[r], kc[r], blk);
-                else ks[r] += blk;
-            }
-        }
-        // order this thread's generic accesses of the buffer before any later bulk refill
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();   // every thread is done with this buffer
-        if (src != nullptr && threadIdx.x == 0 && kt + 2 < sm.n_tiles) {
-            issue_tile(sm, src, n_pad, kt + 2, bar);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < R; ++r) tot[r] = ks[r] - kc[r];
-    return true;
-}
-
-// Reduce the lane sums into part[row][split] and the block's sum_j u_j (returned).
-template <int R, int GJ>
-__device__ __forceinline__ float gj_reduce(const DenseSmem &sm, const float (&tot)[R], float Us, float Uc, int rg,
-                                           int cs, int lane, float *red_s, float *red_c, float *U_sh) {
-    const int warp = threadIdx.x >> 5, W = blockDim.x >> 5;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        float v = tot[r];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) sm.part[(rg * R + r) * GJ + cs] = v;
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        Us += __shfl_xor_sync(0xffffffffu, Us, off);
-        Uc += __shfl_xor_sync(0xffffffffu, Uc, off);
-    }
-    if (lane == 0) {
-        red_s[warp] = Us;
-        red_c[warp] = Uc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f, cc = 0.0f;
-        for (int w = 0; w < W; ++w) kahan_add(s, cc, red_s[w] - red_c[w]);
-        *U_sh = s - cc;
-    }
-    __syncthreads();
-    return *U_sh;
-}
-
-// Gap current of local row rr (after gj_reduce).
-template <int GJ>
-__device__ __forceinline__ float row_current(const DenseSmem &sm, int rr, float u_i, int n, float U, float g) {
-    float S = 0.0f;
-#pragma unroll
-    for (int k = 0; k < GJ; ++k) S += sm.part[rr * GJ + k];
-    const float lin = fmaf((float)n, u_i, -U);
-    return g * (1.0f / GJ_SCALE) * fmaf(0.8f, S, 0.2f * lin);
-}
 
 // ---- one launch per step ----------------------------------------------------------------
 // Launch bounds: up to 1024 threads (64 registers) when R <= 2, else 768.

@@ -12,6 +12,7 @@ namespace ion {
 // to a multiple of PAD_J floats with a sentinel voltage far from any physiological
 // value, so padded pairs contribute exactly 0 to the exponential sum.
 constexpr int TJ = 8192;
+constexpr int CSR_CHUNK = 32768;   // floats of V_dend per shared-memory chunk (128 KB)
 constexpr int PAD_J = 256;
 constexpr float PAD_VOLT = 1.0e7f;
 
@@ -94,6 +95,12 @@ struct CellArgs {
 // launchers (return the CUDA launch status)
 cudaError_t launch_dense_step(const DenseArgs &a, int rows_per_warp, int warps, int col_splits, cudaStream_t st);
 cudaError_t launch_csr_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, cudaStream_t st);
+cudaError_t prepare_csr_step();
+cudaError_t launch_csr_chunk_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *mid,
+                                  int n_chunks, bool prepare, cudaStream_t st);
+cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
+                                    int32_t *mid, cudaStream_t st);
+size_t csr_chunk_smem_bytes(int n_pad, int rows);
 cudaError_t launch_cell_step(const CellArgs &a, cudaStream_t st);
 cudaError_t launch_advance(int64_t *t_dev, int64_t k, cudaStream_t st);
 cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);

@@ -9,8 +9,11 @@
 #include "ion_kernels.cuh"
 
 struct ion_sim {
-    // network
+    // network (batches: n = padded total, n_user = cells in the user's numbering, and
+    // d_map[user cell] = padded cell)
     int32_t n = 0, kind = 0, n_pad = 0;
+    int64_t n_user = 0;
+    int32_t *d_map = nullptr;
     int64_t stride = 0;
     float g = 0.0f;                 // dense pair weight / CSR default weight
     int64_t nnz = 0;
@@ -50,6 +53,9 @@ struct ion_sim {
     int persist_R = 0, persist_W = 0, persist_GJ = 1;
     int device = 0, sms = 1;
     int dense_R = 1, dense_W = 4, dense_GJ = 1, csr_SW = 8, csr_rows = 256;
+    int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk
+    int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
+    int32_t *d_mid = nullptr;       // interior chunk boundaries per row
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     bool no_graph = false;
@@ -76,6 +82,11 @@ float *ion_field_ptr(ion_sim *s, int32_t field);
 ion_status ion_validate_csr(int32_t n, const ion_conn *c);
 void ion_choose_dense_shape(int n, int sms, int *R, int *W, int *GJ);
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
+ion_status ion_setup_csr_staging(ion_sim *s, int mode);
 void ion_sim_free_device(ion_sim *s);
 // per-flag setup of the extensions (ion_ext.cu)
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p);
+// batch state I/O in the user's numbering (ion_batch.cu)
+ion_status ion_batch_read(ion_sim *s, int32_t field, float *out);
+ion_status ion_batch_write(ion_sim *s, int32_t field, const float *in);
+int32_t ion_batch_map_cell(ion_sim *s, int64_t user_cell);

@@ -69,8 +69,9 @@ class ion_input(ctypes.Structure):
 
 class ion_tune(ctypes.Structure):
     _fields_ = [("dense_rows_per_warp", ctypes.c_int32), ("dense_warps", ctypes.c_int32),
-                ("dense_col_splits", ctypes.c_int32), ("csr_lanes_per_row", ctypes.c_int32), ("csr_rows_per_cta", ctypes.c_int32),
-                ("batch_tile_pairs", ctypes.c_int32)]
+                ("dense_col_splits", ctypes.c_int32), ("csr_lanes_per_row", ctypes.c_int32),
+                ("csr_rows_per_cta", ctypes.c_int32), ("csr_lanes_scale", ctypes.c_int32),
+                ("csr_staging", ctypes.c_int32)]
 
 
 class ion_surrogate_weights(ctypes.Structure):
@@ -105,6 +106,7 @@ _SIGS = {
     "ion_set_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "ion_read_trace": (ctypes.c_int, [ctypes.c_void_p, c_f32p, ctypes.c_int64, c_i64p]),
     "ion_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ion_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ion_tune)]),
     "ion_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "ion_set_step_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "ion_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
@@ -342,6 +344,13 @@ def ion_read_trace(h, n: int, max_samples: int) -> np.ndarray:
     got = ctypes.c_int64()
     _check(lib().ion_read_trace(h, _ptr(out, ctypes.c_float), int(max_samples), ctypes.byref(got)), h)
     return out[:got.value]
+
+
+def ion_autotune(h, steps: int = 20) -> dict:
+    """Time candidate launch shapes and keep the fastest; returns the chosen table."""
+    t = ion_tune()
+    _check(lib().ion_autotune(h, int(steps), ctypes.byref(t)), h)
+    return {k: int(getattr(t, k)) for k, _ in ion_tune._fields_}
 
 
 def ion_step_count(h) -> int:

@@ -1,0 +1,185 @@
+"""Batched networks (one launch per step over many networks) against the FP64 oracle run
+of each network alone, plus the autotuner (it must leave the simulation untouched)."""
+import numpy as np
+import pytest
+
+from paper_1612_01501_gb300 import inputs
+from paper_1612_01501_gb300 import ion
+
+from helpers import STEP_RTOL, TRAJ_MV, csr_abs_scale, step_rel_err, sum_abs_dv
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01501_gb300 import build
+    build.build()
+    return torch
+
+
+def _nets(specs):
+    out = []
+    for sp in specs:
+        b = inputs.batch_network(sp)
+        b["spec"] = sp
+        out.append(b)
+    return out
+
+
+def _batch_inputs(O, nets):
+    """Concatenated FP32 initial state and pulse table in the batch's cell numbering."""
+    states, cells, beg, end, amp = [], [], [], [], []
+    off = 0
+    for b in nets:
+        S = O.default_state(b["n"])
+        S[O.F["V_dend"]] += b["jitter"]
+        states.append(S.astype(np.float32))
+        p = b["pulses"]
+        cells.append(p[0] + off)
+        beg.append(p[1]); end.append(p[2]); amp.append(p[3])
+        off += b["n"]
+    S0 = np.concatenate(states, axis=1)
+    pul = (np.concatenate(cells).astype(np.int32), np.concatenate(beg), np.concatenate(end), np.concatenate(amp))
+    return S0, pul
+
+
+def _ion_nets(nets):
+    out = []
+    for b in nets:
+        if b["kind"] == "dense":
+            out.append(dict(n=b["n"], kind=ion.DENSE_UNIFORM, g=b["g"]))
+        elif b["kind"] == "csr":
+            out.append(dict(n=b["n"], kind=ion.CSR, row_ptr=b["row_ptr"], col=b["col"], w=b["w"]))
+        else:
+            out.append(dict(n=b["n"], kind=ion.NO_GJ))
+    return out
+
+
+def _oracle_net(O, b, S0, steps, pulses):
+    kind = {"dense": O.DENSE, "csr": O.CSR, "nogj": O.NOGJ}[b["kind"]]
+    return O.run(S0.astype(np.float64), steps, kind=kind, g=b.get("g", 0.0), row_ptr=b.get("row_ptr"),
+                 col=b.get("col"), w=None if b.get("w") is None else b["w"].astype(np.float64), pulses=pulses,
+                 threads=max(1, O.max_threads()))[0]
+
+
+def _mixed_specs():
+    return [dict(n=37, kind="dense", k=37, g_ref=0.03, seed=5), dict(n=300, kind="csr", k=12, g_ref=0.05, seed=6),
+            dict(n=1000, kind="dense", k=1000, g_ref=0.08, seed=7), dict(n=257, kind="csr", k=100, g_ref=0.02, seed=8),
+            dict(n=4096, kind="dense", k=4096, g_ref=0.01, seed=9), dict(n=33, kind="csr", k=8, g_ref=0.04, seed=10)]
+
+
+def test_batch_matches_each_network_alone(cuda, O):
+    nets = _nets(_mixed_specs())
+    S0, pul = _batch_inputs(O, nets)
+    with_h = ion.ion_create_batch(_ion_nets(nets), init_state=S0)
+    try:
+        ion.ion_set_input(with_h, pul)
+        ion.ion_step(with_h, 600)            # pulses at 20-30 ms = steps 400..600
+        got = ion.ion_read_state(with_h, S0.shape[1])
+    finally:
+        ion.ion_destroy(with_h)
+    off = 0
+    for b in nets:
+        n = b["n"]
+        ref = _oracle_net(O, b, S0[:, off:off + n], 600, b["pulses"])
+        assert np.abs(got[:3, off:off + n] - ref[:3]).max() <= TRAJ_MV, (b["spec"], np.abs(got[:3, off:off + n] - ref[:3]).max())
+        off += n
+
+
+def test_batch_one_step_error(cuda, O):
+    nets = _nets(_mixed_specs())
+    S0, pul = _batch_inputs(O, nets)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0)
+    try:
+        ion.ion_step(h, 1)
+        got = ion.ion_read_state(h, S0.shape[1])
+    finally:
+        ion.ion_destroy(h)
+    off = 0
+    for b in nets:
+        n = b["n"]
+        ref = _oracle_net(O, b, S0[:, off:off + n], 1, None)
+        if b["kind"] == "dense":
+            scale = b["g"] * sum_abs_dv(S0[0, off:off + n])
+        else:
+            scale = csr_abs_scale(b["row_ptr"], b["col"], b["w"], S0[0, off:off + n])
+        err = step_rel_err(got[:, off:off + n], ref, scale)
+        assert err.max() <= STEP_RTOL, (b["spec"], err.max(axis=1))
+        off += n
+
+
+def test_c4_batch_of_256_sampled_against_oracle(cuda, O):
+    specs = inputs.batch_specs()
+    nets = _nets(specs)
+    S0, pul = _batch_inputs(O, nets)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, graph_steps=50)
+    try:
+        ion.ion_set_input(h, pul)
+        ion.ion_step(h, 200)
+        got = ion.ion_read_state(h, S0.shape[1])
+    finally:
+        ion.ion_destroy(h)
+    offs = np.concatenate([[0], np.cumsum([b["n"] for b in nets])])
+    dense = [i for i, b in enumerate(nets) if b["kind"] == "dense"]
+    csr = [i for i, b in enumerate(nets) if b["kind"] == "csr"]
+    pick = [min(dense, key=lambda i: nets[i]["n"]), min(csr, key=lambda i: nets[i]["n"]),
+            max(csr, key=lambda i: nets[i]["n"]), sorted(dense, key=lambda i: nets[i]["n"])[len(dense) // 2]]
+    for i in pick:
+        b = nets[i]
+        ref = _oracle_net(O, b, S0[:, offs[i]:offs[i + 1]], 200, b["pulses"])
+        assert np.abs(got[:3, offs[i]:offs[i + 1]] - ref[:3]).max() <= TRAJ_MV, b["spec"]
+    assert np.all(np.isfinite(got))
+
+
+def test_autotune_leaves_state_untouched_and_results_agree(cuda, O):
+    nets = _nets(_mixed_specs())
+    S0, pul = _batch_inputs(O, nets)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0)
+    try:
+        ion.ion_set_input(h, pul)
+        ion.ion_step(h, 10)
+        before = ion.ion_read_state(h, S0.shape[1])
+        table = ion.ion_autotune(h, 5)
+        assert ion.ion_step_count(h) == 10
+        np.testing.assert_array_equal(ion.ion_read_state(h, S0.shape[1]), before)
+        assert table["dense_rows_per_warp"] in (1, 2, 4, 8) and 1 <= table["csr_rows_per_cta"] <= 256
+        ion.ion_step(h, 590)
+        got = ion.ion_read_state(h, S0.shape[1])
+    finally:
+        ion.ion_destroy(h)
+    off = 0
+    for b in nets:
+        n = b["n"]
+        ref = _oracle_net(O, b, S0[:, off:off + n], 600, b["pulses"])
+        assert np.abs(got[:3, off:off + n] - ref[:3]).max() <= TRAJ_MV
+        off += n
+
+
+@pytest.mark.parametrize("kind", ["dense", "csr"])
+def test_autotune_single_network(cuda, O, kind):
+    n = 4000
+    if kind == "dense":
+        kw = dict(kind=ion.DENSE_UNIFORM, g=inputs.junction_weight(0.04, n))
+    else:
+        rp, col = inputs.random_symmetric_csr(n, 60, 4)
+        kw = dict(kind=ion.CSR, row_ptr=rp, col=col, w=np.full(len(col), inputs.junction_weight(0.04, 60), np.float32))
+    S0 = O.default_state(n)
+    S0[0] += inputs.vdend_jitter(n, 4)
+    S0 = S0.astype(np.float32)
+    sim = ion.Simulation(n, init_state=S0, **kw)
+    try:
+        table = ion.ion_autotune(sim.h, 5)
+        assert sim.t == 0
+        np.testing.assert_array_equal(sim.state(), S0)
+        sim.step(100)
+        got = sim.state()
+    finally:
+        sim.close()
+    assert any(v != 0 for v in table.values())
+    b = dict(kind=kind, g=kw.get("g", 0.0), row_ptr=kw.get("row_ptr"), col=kw.get("col"), w=kw.get("w"))
+    ref = _oracle_net(O, b, S0, 100, None)
+    assert np.abs(got[:3] - ref[:3]).max() <= TRAJ_MV

@@ -291,3 +291,51 @@ def test_write_then_read_roundtrip(torch_cuda, O):
         np.testing.assert_array_equal(sim.state(), S)
         sim.write(S[5] * 0 + 0.25, field=5)
         assert np.all(sim.state(5) == 0.25)
+
+
+@pytest.mark.parametrize("sw,rows", [(1, 37), (2, 256), (8, 100), (32, 7)])
+def test_csr_launch_shapes_agree(torch_cuda, O, sw, rows):
+    """Every lanes-per-row / rows-per-CTA choice gives the oracle's step (ragged CTAs)."""
+    n = 3001
+    rp, col = inputs.random_symmetric_csr(n, 24, 13)
+    w = np.full(len(col), inputs.junction_weight(0.04, 24), np.float32)
+    err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=5,
+                         tune=dict(csr_lanes_per_row=sw, csr_rows_per_cta=rows))
+    assert err.max() <= STEP_RTOL
+
+
+def test_gj_csr_unaligned_and_unweighted(torch_cuda, O):
+    """Index/weight arrays that are not 16-byte aligned take the scalar-load path; a NULL
+    weight array means every weight is g_c."""
+    torch = torch_cuda
+    n = 4000
+    rp, col = inputs.random_symmetric_csr(n, 50, 17)
+    vd = (-60.0 + inputs.vdend_jitter(n, 19, 20.0)).astype(np.float32)
+    w = inputs.uniform(inputs.stream_seed(3, "w"), len(col), 0.001, 0.05).astype(np.float32)
+    T = lambda a: torch.from_numpy(a).cuda()
+    col_u = torch.zeros(len(col) + 1, dtype=torch.int32, device="cuda")
+    col_u[1:] = T(col)
+    w_u = torch.zeros(len(col) + 1, dtype=torch.float32, device="cuda")
+    w_u[1:] = T(w)
+    ic = torch.empty(n, dtype=torch.float32, device="cuda")
+    ion.ion_gj_csr(T(vd), T(rp), col_u[1:], w_u[1:], 0.0, ic)
+    torch.cuda.synchronize()
+    ref = O.gj_csr(rp, col, w.astype(np.float64), vd.astype(np.float64))
+    scale = csr_abs_scale(rp, col, w, vd)
+    assert np.all(np.abs(ic.cpu().numpy() - ref) <= 2e-6 * scale + 1e-30)
+    g = 0.02
+    ion.ion_gj_csr(T(vd), T(rp), T(col), None, g, ic)
+    torch.cuda.synchronize()
+    ref = O.gj_csr(rp, col, np.full(len(col), np.float64(np.float32(g))), vd.astype(np.float64))
+    scale = csr_abs_scale(rp, col, np.full(len(col), g), vd)
+    assert np.all(np.abs(ic.cpu().numpy() - ref) <= 2e-6 * scale + 1e-30)
+
+
+@pytest.mark.parametrize("n,k,staging", [(40000, 64, 0), (40000, 64, 1), (3001, 40, 2), (70000, 12, 2)])
+def test_csr_shared_memory_staging(torch_cuda, O, n, k, staging):
+    """V_dend staged in shared memory chunk by chunk (two or three 128 KB chunks, or one),
+    or gathered through L1/L2: both match the oracle's step."""
+    rp, col = inputs.random_symmetric_csr(n, k, 23)
+    w = np.full(len(col), inputs.junction_weight(0.04, k), np.float32)
+    err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=3, tune=dict(csr_staging=staging))
+    assert err.max() <= STEP_RTOL
