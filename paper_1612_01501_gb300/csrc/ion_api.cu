@@ -235,13 +235,17 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
 }
 
 // Shared-memory staging of V_dend for a CSR network (mode 0: choose, 1: off, 2: on).
-// Staging pays once the gathers dominate: on for a mean degree of 32 or more in networks
-// of at least 4096 cells.  One CTA per SM owns ceil(n / SMs) rows (at most 1024).  Only
+// Staging pays when the index/weight arrays stream from HBM (they do not fit in the 129 MB
+// L2 next to the state) and rows are long enough to amortise staging every chunk per CTA:
+// measured on the 65 536-cell network, k = 1000 went from 0.45 to 0.69 of HBM bandwidth
+// while k = 100 (L2-resident) got slower.  One CTA per SM owns ceil(n / SMs) rows (at most
+// 1024).  Only
 // CSR arrays copied from the host are staged: their columns were checked to be sorted
 // and in range, which the chunk boundaries rely on.
 ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     const double deg = s->n > 0 ? (double)s->nnz / s->n : 0.0;
-    const bool on = mode == 2 || (mode == 0 && deg >= 32.0 && s->n >= 4096);
+    const double csr_bytes = 8.0 * (double)s->nnz;
+    const bool on = mode == 2 || (mode == 0 && deg >= 64.0 && csr_bytes > 96.0e6);
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
     if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr) return ION_OK;

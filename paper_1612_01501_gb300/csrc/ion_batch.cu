@@ -403,6 +403,7 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     const ion_tune *tu = (const ion_tune *)params->tune;
     if (tu && tu->dense_rows_per_warp > 0) X->R = tu->dense_rows_per_warp;
     if (tu && tu->csr_rows_per_cta > 0) X->csr_rows = tu->csr_rows_per_cta;
+    if (tu && tu->csr_lanes_scale != 0) X->sw_scale = tu->csr_lanes_scale > 0 ? 1 : -1;
     if ((X->R != 1 && X->R != 2 && X->R != 4 && X->R != 8) || X->csr_rows < 1 || X->csr_rows > 256)
         return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad tile shape override"));
     // global CSR over the padded index space
@@ -539,7 +540,7 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         bt.dense_warps = 8;
         bt.dense_col_splits = 1;
         bt.csr_rows_per_cta = brows;
-        bt.csr_lanes_per_row = bsc;   // scale of the degree-based choice: 0, +1 (x2), -1 (/2)
+        bt.csr_lanes_scale = bsc;     // scale of the degree-based choice: 0, +1 (x2), -1 (/2)
     } else if (s->kind == ION_DENSE_UNIFORM) {
         int R0, W0, G0;
         ion_choose_dense_shape(s->n, s->sms, &R0, &W0, &G0);

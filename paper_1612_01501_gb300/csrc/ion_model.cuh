@@ -131,7 +131,31 @@ struct CellNext {  // the 18 words it writes (g_CaL is constant)
 // x + dt (xinf - x) / tau
 __device__ __forceinline__ float relax(float x, Rate g, float dt) { return fmaf(dt * g.inv_tau, g.xinf - x, x); }
 
-__device__ __forceinline__ CellNext cell_step(const ModelF &P, const Cell &c, float ic, float iapp) {
+// Rates of one cell's gates (the m_s / m_a entries only use xinf).
+struct CellRates {
+    Rate r, s, q, k, l, ms, hs, ns, xs, ma, ha, xa;
+};
+
+__device__ __forceinline__ CellRates exact_rates(const Cell &c) {
+    CellRates g;
+    g.r = rate_r(c.vd);
+    g.s = rate_s(c.ca);
+    g.q = rate_q(c.vd);
+    g.k = rate_k(c.vs);
+    g.l = rate_l(c.vs);
+    g.ms = Rate{minf_na(c.vs), 0.0f};
+    g.hs = rate_hs(c.vs);
+    g.ns = rate_ns(c.vs);
+    g.xs = rate_x(c.vs);
+    g.ma = Rate{minf_na(c.va), 0.0f};
+    g.ha = rate_ha(c.va);
+    g.xa = rate_x(c.va);
+    return g;
+}
+
+// One explicit-Euler step of one cell given its gates' rates (exact or learned).
+__device__ __forceinline__ CellNext cell_step_rates(const ModelF &P, const Cell &c, float ic, float iapp,
+                                                    const CellRates &g) {
     CellNext o;
     const float dt = P.dt;
     // dendrite
@@ -142,13 +166,13 @@ __device__ __forceinline__ CellNext cell_step(const ModelF &P, const Cell &c, fl
     const float I_ds = P.g_ds * (c.vd - c.vs);
     o.vd = fmaf(P.dt_cm, iapp - I_CaH - I_KCa - I_h - I_ld - I_ds - ic, c.vd);
     o.ca = fmaf(dt, -P.ca_in * I_CaH - P.ca_out * c.ca, c.ca);
-    o.r = relax(c.r, rate_r(c.vd), dt);
-    o.s = relax(c.s, rate_s(c.ca), dt);
-    o.q = relax(c.q, rate_q(c.vd), dt);
+    o.r = relax(c.r, g.r, dt);
+    o.s = relax(c.s, g.s, dt);
+    o.q = relax(c.q, g.q, dt);
     o.icah = I_CaH;
     o.ic = ic;
     // soma
-    const float ms = minf_na(c.vs);
+    const float ms = g.ms.xinf;
     const float k3 = c.k * c.k * c.k;
     const float n2 = c.ns * c.ns, x2 = c.xs * c.xs;
     const float I_CaL = c.gcal * k3 * c.l * (c.vs - P.VCa);
@@ -159,14 +183,14 @@ __device__ __forceinline__ CellNext cell_step(const ModelF &P, const Cell &c, fl
     const float I_sd = P.g_sd * (c.vs - c.vd);
     const float I_sa = P.g_sa * (c.vs - c.va);
     o.vs = fmaf(-P.dt_cm, I_CaL + I_Nas + I_Kdr + I_Ks + I_ls + I_sd + I_sa, c.vs);
-    o.k = relax(c.k, rate_k(c.vs), dt);
-    o.l = relax(c.l, rate_l(c.vs), dt);
+    o.k = relax(c.k, g.k, dt);
+    o.l = relax(c.l, g.l, dt);
     o.ms = ms;
-    o.hs = relax(c.hs, rate_hs(c.vs), dt);
-    o.ns = relax(c.ns, rate_ns(c.vs), dt);
-    o.xs = relax(c.xs, rate_x(c.vs), dt);
+    o.hs = relax(c.hs, g.hs, dt);
+    o.ns = relax(c.ns, g.ns, dt);
+    o.xs = relax(c.xs, g.xs, dt);
     // axon
-    const float ma = minf_na(c.va);
+    const float ma = g.ma.xinf;
     const float xa2 = c.xa * c.xa;
     const float I_Naa = P.gNaa * ma * ma * ma * c.ha * (c.va - P.VNa);
     const float I_Ka = P.gKa * xa2 * xa2 * (c.va - P.VK);
@@ -174,9 +198,13 @@ __device__ __forceinline__ CellNext cell_step(const ModelF &P, const Cell &c, fl
     const float I_as = P.g_as * (c.va - c.vs);
     o.va = fmaf(-P.dt_cm, I_Naa + I_Ka + I_la + I_as, c.va);
     o.ma = ma;
-    o.ha = relax(c.ha, rate_ha(c.va), dt);
-    o.xa = relax(c.xa, rate_x(c.va), dt);
+    o.ha = relax(c.ha, g.ha, dt);
+    o.xa = relax(c.xa, g.xa, dt);
     return o;
+}
+
+__device__ __forceinline__ CellNext cell_step(const ModelF &P, const Cell &c, float ic, float iapp) {
+    return cell_step_rates(P, c, ic, iapp, exact_rates(c));
 }
 
 // ---- SoA access -----------------------------------------------------------------
