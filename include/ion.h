@@ -312,10 +312,14 @@ ion_status ion_cell_update(float *state, int32_t n, const float *ic, const float
 ion_status ion_probe_peak(int32_t what, int32_t iters, void *cuda_stream, double *rate_out);
 
 /* ---- learned surrogate of the rate functions ------------------------------------ */
-
-/* MLP 2 -> 64 -> 64 -> 24 (x_inf and log tau of each of the 12 gates) with tanh hidden
- * units, used in place of the exact rate functions when ION_FLAG_SURROGATE is set.
- * Weights row-major [out][in]; FP32 master copy. */
+/* Not in the paper.  An MLP (V, [Ca]) -> 64 tanh -> 64 tanh -> 24 outputs stands in for
+ * the gates' rate functions when ION_FLAG_SURROGATE is set (ion_params.surrogate points
+ * at an ion_surrogate_weights): output 2g is x_inf of gate g (order r s q k l m_s h_s n_s
+ * x_s m_a h_a x_a), output 2g+1 is ln(tau_g) (unused for m_s, m_a).  Inputs are
+ * x = ((V - in_shift[0]) in_scale[0], (ln [Ca] - in_shift[1]) in_scale[1]); outputs are
+ * y = y' out_scale + out_shift.  Weights row-major [out][in], FP32; inference converts
+ * the 64x64 and 64x24 layers to BF16 and runs them on the tensor cores (FP32
+ * accumulation), fused with the cell update. */
 #define ION_MLP_IN 2
 #define ION_MLP_HID 64
 #define ION_MLP_OUT 24
@@ -323,26 +327,42 @@ typedef struct {
     float w1[ION_MLP_HID * ION_MLP_IN], b1[ION_MLP_HID];
     float w2[ION_MLP_HID * ION_MLP_HID], b2[ION_MLP_HID];
     float w3[ION_MLP_OUT * ION_MLP_HID], b3[ION_MLP_OUT];
-    float in_shift[ION_MLP_IN], in_scale[ION_MLP_IN];   /* x' = (x - shift) * scale */
-    float out_shift[ION_MLP_OUT], out_scale[ION_MLP_OUT]; /* y = y' * scale + shift   */
+    float in_shift[ION_MLP_IN], in_scale[ION_MLP_IN];
+    float out_shift[ION_MLP_OUT], out_scale[ION_MLP_OUT];
 } ion_surrogate_weights;
 
 typedef struct {
-    int64_t n_samples;   /* training set size (e.g. 1e6)                            */
-    int32_t epochs;
-    int32_t batch;       /* minibatch size, multiple of 128                         */
-    float lr;            /* Adam step size                                          */
-    uint64_t seed;
-    float v_lo, v_hi;    /* V range, mV                                             */
-    float ca_lo, ca_hi;  /* [Ca] range (log-uniform)                                */
+    int64_t n_samples;   /* training set size (e.g. 1e6), >= 256                    */
+    int32_t epochs;      /* passes over the set (each with its own reshuffle)       */
+    int32_t batch;       /* minibatch size, a multiple of 128, <= n_samples          */
+    float lr;            /* Adam step size (cosine-decayed to 1 % over the run)     */
+    uint64_t seed;       /* samples and initial weights                             */
+    float v_lo, v_hi;    /* V range, mV (uniform)                                   */
+    float ca_lo, ca_hi;  /* [Ca] range (log-uniform), > 0                           */
     void *cuda_stream;
 } ion_train_cfg;
 
-/* Train the surrogate on the GPU from samples of the exact FP32 rate functions.
- * weights_out: host struct, filled on success; final_loss (nullable) gets the mean
- * squared error of the last epoch. */
+/* Train the surrogate on the GPU: draw n_samples (V, [Ca]) on the device, label them with
+ * the exact FP32 rate functions, normalise (per-output mean / standard deviation), fit
+ * by minibatch Adam with the library's own forward / backward kernels (FP32, partial
+ * gradients summed in a fixed order).  weights_out: host struct, filled on success;
+ * final_loss (nullable): mean masked squared error of the last epoch, normalised units.
+ * Synchronises the stream. */
 ion_status ion_surrogate_train(const ion_train_cfg *cfg, ion_surrogate_weights *weights_out,
                                float *final_loss);
+
+/* Gradient of the training loss L = sum_{s,o} mask_o (y_so - t_so)^2 / (B sum(mask)) for
+ * one batch, computed by the training kernels: x (B x 2, normalised inputs), t (B x 24,
+ * normalised targets), mask (24) are host arrays; grad receives dL/dparams in the
+ * weights' layout (w1..b3; the normalisation fields are left untouched); loss
+ * (nullable) receives L.  Synchronises. */
+ion_status ion_surrogate_grad(const ion_surrogate_weights *weights, const float *x, const float *t,
+                              const float *mask, int32_t B, ion_surrogate_weights *grad, float *loss);
+
+/* Evaluate the surrogate on the tensor cores (BF16 weights and activations, FP32
+ * accumulation) for n host pairs (V[i], ca[i]); out (host, n x 24) in physical units. */
+ion_status ion_surrogate_eval(const ion_surrogate_weights *weights, const float *V, const float *ca,
+                              int64_t n, float *out);
 
 #ifdef __cplusplus
 }

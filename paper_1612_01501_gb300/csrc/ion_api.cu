@@ -295,6 +295,7 @@ void ion_sim_free_device(ion_sim *s) {
     cudaFree(s->d_trace);
     cudaFree(s->d_ic);
     cudaFree(s->d_mid);
+    cudaFree(s->d_mlp);
     s->extra_free(s);
 }
 

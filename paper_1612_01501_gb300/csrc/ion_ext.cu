@@ -64,7 +64,7 @@ static bool choose_persist_shape(ion_sim *s) {
 
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
     s->debug_delay_ns = p->debug_delay_ns;
-    if (s->flags & ION_FLAG_SURROGATE) return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "surrogate: not built");
+    if (s->flags & ION_FLAG_SURROGATE) return ion_setup_surrogate(s, p);
     if ((s->flags & ION_FLAG_PERSISTENT) && s->kind == ION_DENSE_UNIFORM && !(s->flags & ION_FLAG_SPLIT)) {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
@@ -81,7 +81,3 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
     return ION_OK;
 }
 
-extern "C" ion_status ion_surrogate_train(const ion_train_cfg *cfg, ion_surrogate_weights *w, float *loss) {
-    (void)cfg; (void)w; (void)loss;
-    return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_surrogate_train: not built");
-}

@@ -56,6 +56,7 @@ struct ion_sim {
     int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk
     int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
     int32_t *d_mid = nullptr;       // interior chunk boundaries per row
+    void *d_mlp = nullptr;          // packed surrogate weights (ION_FLAG_SURROGATE)
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     bool no_graph = false;
@@ -90,3 +91,5 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p);
 ion_status ion_batch_read(ion_sim *s, int32_t field, float *out);
 ion_status ion_batch_write(ion_sim *s, int32_t field, const float *in);
 int32_t ion_batch_map_cell(ion_sim *s, int64_t user_cell);
+// surrogate (ion_mlp.cu)
+ion_status ion_setup_surrogate(ion_sim *s, const ion_params *p);

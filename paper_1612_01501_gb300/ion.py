@@ -123,6 +123,10 @@ _SIGS = {
                                       ctypes.POINTER(ctypes.c_double)]),
     "ion_surrogate_train": (ctypes.c_int, [ctypes.POINTER(ion_train_cfg), ctypes.POINTER(ion_surrogate_weights),
                                            c_f32p]),
+    "ion_surrogate_grad": (ctypes.c_int, [ctypes.POINTER(ion_surrogate_weights), c_f32p, c_f32p, c_f32p,
+                                          ctypes.c_int32, ctypes.POINTER(ion_surrogate_weights), c_f32p]),
+    "ion_surrogate_eval": (ctypes.c_int, [ctypes.POINTER(ion_surrogate_weights), c_f32p, c_f32p, ctypes.c_int64,
+                                          c_f32p]),
 }
 
 _lib = None
@@ -421,6 +425,51 @@ def ion_surrogate_train(n_samples=1_000_000, epochs=20, batch=1024, lr=1e-3, see
     loss = ctypes.c_float()
     _check(lib().ion_surrogate_train(ctypes.byref(cfg), ctypes.byref(w), ctypes.byref(loss)))
     return w, float(loss.value)
+
+
+_WFIELDS = ("w1", "b1", "w2", "b2", "w3", "b3")
+
+
+def weights_from_dict(p: dict, in_shift=(0.0, 0.0), in_scale=(1.0, 1.0), out_shift=None, out_scale=None):
+    """ion_surrogate_weights from arrays w1 (64,2), b1, w2 (64,64), b2, w3 (24,64), b3."""
+    w = ion_surrogate_weights()
+    for k in _WFIELDS:
+        getattr(w, k)[:] = [float(v) for v in np.asarray(p[k], np.float32).reshape(-1)]
+    w.in_shift[:] = list(map(float, in_shift))
+    w.in_scale[:] = list(map(float, in_scale))
+    w.out_shift[:] = [0.0] * MLP_OUT if out_shift is None else list(map(float, out_shift))
+    w.out_scale[:] = [1.0] * MLP_OUT if out_scale is None else list(map(float, out_scale))
+    return w
+
+
+def weights_to_dict(w) -> dict:
+    shapes = {"w1": (MLP_HID, MLP_IN), "b1": (MLP_HID,), "w2": (MLP_HID, MLP_HID), "b2": (MLP_HID,),
+              "w3": (MLP_OUT, MLP_HID), "b3": (MLP_OUT,)}
+    d = {k: np.array(getattr(w, k)[:], np.float32).reshape(shapes[k]) for k in _WFIELDS}
+    for k in ("in_shift", "in_scale", "out_shift", "out_scale"):
+        d[k] = np.array(getattr(w, k)[:], np.float32)
+    return d
+
+
+def ion_surrogate_grad(w, x, t, mask):
+    """(loss, gradient dict) of one batch, computed by the training kernels."""
+    x = np.ascontiguousarray(x, np.float32)
+    t = np.ascontiguousarray(t, np.float32)
+    mask = np.ascontiguousarray(mask, np.float32)
+    g = ion_surrogate_weights()
+    L = ctypes.c_float()
+    _check(lib().ion_surrogate_grad(ctypes.byref(w), _ptr(x, ctypes.c_float), _ptr(t, ctypes.c_float),
+                                    _ptr(mask, ctypes.c_float), int(x.shape[0]), ctypes.byref(g), ctypes.byref(L)))
+    return float(L.value), weights_to_dict(g)
+
+
+def ion_surrogate_eval(w, V, ca) -> np.ndarray:
+    V = np.ascontiguousarray(V, np.float32)
+    ca = np.ascontiguousarray(ca, np.float32)
+    out = np.zeros((len(V), MLP_OUT), np.float32)
+    _check(lib().ion_surrogate_eval(ctypes.byref(w), _ptr(V, ctypes.c_float), _ptr(ca, ctypes.c_float), len(V),
+                                    _ptr(out, ctypes.c_float)))
+    return out
 
 
 class Simulation:

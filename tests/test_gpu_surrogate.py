@@ -1,0 +1,112 @@
+"""Learned surrogate of the rate functions: GPU training kernels against the FP64 MLP
+oracle (gradients), tensor-core inference against an FP64 forward pass, the trained
+network against the exact rate functions, and a simulation with learned rates against the
+exact FP32 method (trace and spike-time error are reported, with loose bounds)."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+from paper_1612_01501_gb300 import inputs
+from paper_1612_01501_gb300 import ion
+
+pytestmark = pytest.mark.gpu
+CA_RANGE = (1.36, 13.5)       # the [Ca] seen in 1 s of the 64-cell network, widened x0.5 / x2
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1612_01501_gb300 import build
+    build.build()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def trained(cuda):
+    w, loss = ion.ion_surrogate_train(n_samples=1 << 18, epochs=12, batch=2048, lr=2e-3, seed=7, v_lo=-100.0,
+                                      v_hi=50.0, ca_lo=CA_RANGE[0], ca_hi=CA_RANGE[1])
+    print(f"surrogate training: final normalised loss {loss:.3e}")
+    return w, loss
+
+
+@pytest.mark.parametrize("B", [128, 300])
+def test_training_gradients_match_fp64_oracle(cuda, B):
+    rng = np.random.default_rng(B)
+    p = mlp.init_params(5, scale=1.5)
+    x = rng.uniform(-1, 1, (B, 2)).astype(np.float32)
+    t = rng.normal(0, 1, (B, 24)).astype(np.float32)
+    mask = np.ones(24, np.float32)
+    mask[[11, 19]] = 0.0
+    w = ion.weights_from_dict({k: v.astype(np.float32) for k, v in p.items()})
+    L, g = ion.ion_surrogate_grad(w, x, t, mask)
+    p32 = {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
+    Lr, gr = mlp.loss_and_grads(p32, x.astype(np.float64), t.astype(np.float64), mask.astype(np.float64))
+    assert L == pytest.approx(Lr, rel=1e-5)
+    for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
+        rel = np.linalg.norm(g[k] - gr[k]) / np.linalg.norm(gr[k])
+        assert rel <= 1e-4, (k, rel)
+
+
+def test_tensor_core_inference_matches_fp64_forward(cuda):
+    p = mlp.init_params(9, scale=1.0)
+    rng = np.random.default_rng(1)
+    V = rng.uniform(-100, 50, 1000).astype(np.float32)
+    ca = np.exp(rng.uniform(np.log(CA_RANGE[0]), np.log(CA_RANGE[1]), 1000)).astype(np.float32)
+    lo, hi = np.log(CA_RANGE[0]), np.log(CA_RANGE[1])
+    w = ion.weights_from_dict({k: v.astype(np.float32) for k, v in p.items()},
+                              in_shift=(mlp.V_CENTER, 0.5 * (lo + hi)), in_scale=(1 / mlp.V_HALF, 2 / (hi - lo)))
+    got = ion.ion_surrogate_eval(w, V, ca)
+    x = mlp.normalise_inputs(V, ca, *CA_RANGE)
+    ref, _ = mlp.forward({k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}, x)
+    err = np.abs(got - ref)
+    # BF16 weights and activations (8-bit mantissa), FP32 accumulation over 64 terms
+    assert err.max() <= 0.05 + 0.02 * np.abs(ref).max(), err.max()
+    assert err.mean() <= 0.01
+
+
+def test_trained_surrogate_fits_the_rate_functions(trained, O):
+    w, loss = trained
+    assert loss < 2e-3
+    rng = np.random.default_rng(11)
+    V = rng.uniform(-100, 50, 4000).astype(np.float32)
+    ca = np.exp(rng.uniform(np.log(CA_RANGE[0]), np.log(CA_RANGE[1]), 4000)).astype(np.float32)
+    got = ion.ion_surrogate_eval(w, V, ca)
+    ref, mask = mlp.gate_targets(V, ca)
+    xinf_err = np.abs(got[:, 0::2] - ref[:, 0::2])
+    lntau_err = np.abs(got[:, 1::2] - ref[:, 1::2])[:, mask[1::2] > 0]
+    print(f"x_inf |err| mean {xinf_err.mean():.2e} max {xinf_err.max():.2e}; "
+          f"ln tau |err| mean {lntau_err.mean():.2e} max {lntau_err.max():.2e}")
+    assert xinf_err.mean() < 0.01 and xinf_err.max() < 0.1
+    assert lntau_err.mean() < 0.05
+
+
+def test_simulation_with_learned_rates(trained, O):
+    """A 4096-cell k = 100 network for 2000 steps with learned vs exact rates: the voltage
+    traces stay close and both stay finite (the numbers are printed; bounds are loose:
+    the surrogate changes the model, it is not a rounding error)."""
+    w, _ = trained
+    n = 4096
+    rp, col = inputs.random_symmetric_csr(n, 100, 2)
+    wts = np.full(len(col), inputs.junction_weight(0.04, 100), np.float32)
+    S0 = O.default_state(n)
+    S0[0] += inputs.vdend_jitter(n, 2)
+    S0 = S0.astype(np.float32)
+    pul = inputs.pulses(inputs.random_subset(n, 0.2, 2), 50.0, 60.0, 6.0)
+    out = []
+    for flags, kw in ((ion.FLAG_KAHAN, {}), (ion.FLAG_KAHAN | ion.FLAG_SURROGATE, dict(surrogate=w))):
+        with ion.Simulation(n, ion.CSR, row_ptr=rp, col=col, w=wts, init_state=S0, flags=flags, **kw) as sim:
+            sim.set_input(pul)
+            ion.ion_set_trace(sim.h, 1, 2000)
+            sim.step(2000)
+            out.append((sim.state(), ion.ion_read_trace(sim.h, n, 2000)))
+    (Se, te), (Ss, ts) = out
+    assert np.all(np.isfinite(Ss))
+    dv = np.abs(Se[:3] - Ss[:3]).max()
+    trace_rms = float(np.sqrt(np.mean((te - ts) ** 2)))
+    se = [len(O.spike_steps(te[:, c])) for c in range(0, n, 64)]
+    ss = [len(O.spike_steps(ts[:, c])) for c in range(0, n, 64)]
+    print(f"surrogate vs exact: max |dV| {dv:.3f} mV, V_axon trace rms {trace_rms:.3f} mV, "
+          f"spikes {sum(se)} vs {sum(ss)} (64 sampled cells)")
+    assert trace_rms < 5.0
