@@ -314,8 +314,9 @@ ion_status ion_probe_peak(int32_t what, int32_t iters, void *cuda_stream, double
 /* ---- learned surrogate of the rate functions ------------------------------------ */
 /* Not in the paper.  An MLP (V, [Ca]) -> 64 tanh -> 64 tanh -> 24 outputs stands in for
  * the gates' rate functions when ION_FLAG_SURROGATE is set (ion_params.surrogate points
- * at an ion_surrogate_weights): output 2g is x_inf of gate g (order r s q k l m_s h_s n_s
- * x_s m_a h_a x_a), output 2g+1 is ln(tau_g) (unused for m_s, m_a).  Inputs are
+ * at an ion_surrogate_weights): output 2g is logit(x_inf) of gate g, clipped to +-15 (gate
+ * order r s q k l m_s h_s n_s x_s m_a h_a x_a), output 2g+1 is ln(tau_g) (unused for
+ * m_s, m_a).  Inputs are
  * x = ((V - in_shift[0]) in_scale[0], (ln [Ca] - in_shift[1]) in_scale[1]); outputs are
  * y = y' out_scale + out_shift.  Weights row-major [out][in], FP32; inference converts
  * the 64x64 and 64x24 layers to BF16 and runs them on the tensor cores (FP32

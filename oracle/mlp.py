@@ -57,16 +57,22 @@ def loss_and_grads(p, x, t, mask):
     return L, g
 
 
+LOGIT_MAX = 15.0
+
+
 def gate_targets(V, ca):
     """Raw targets of every sample from the FP64 rate functions: for gate g, output 2g is
-    x_inf and output 2g+1 is ln(tau) (masked for the instantaneous gates m_s, m_a)."""
+    logit(x_inf) clipped to +-15 and output 2g+1 is ln(tau) (masked for the instantaneous
+    gates m_s, m_a)."""
     V = np.atleast_1d(np.asarray(V, np.float64))
     ca = np.atleast_1d(np.asarray(ca, np.float64))
     out = np.zeros((len(V), N_OUT))
     mask = np.ones(N_OUT)
     for s in range(len(V)):
         xi, ta = _O.rates(V[s], ca[s])
-        out[s, 0::2] = xi
+        with np.errstate(divide="ignore"):
+            lg = np.log(xi) - np.log1p(-np.minimum(xi, 1.0 - 1e-16))
+        out[s, 0::2] = np.clip(lg, -LOGIT_MAX, LOGIT_MAX)
         out[s, 1::2] = np.log(np.where(ta > 0, ta, 1.0))
     for gname in ("m_s", "m_a"):
         mask[2 * _O.GATES.index(gname) + 1] = 0.0
@@ -77,3 +83,7 @@ def normalise_inputs(V, ca, ca_lo, ca_hi):
     lc, lh = np.log(ca_lo), np.log(ca_hi)
     return np.stack([(np.asarray(V, np.float64) - V_CENTER) / V_HALF,
                      (np.log(np.asarray(ca, np.float64)) - 0.5 * (lc + lh)) / (0.5 * (lh - lc))], axis=1)
+
+
+def sigmoid(z):
+    return 1.0 / (1.0 + np.exp(-np.asarray(z, np.float64)))

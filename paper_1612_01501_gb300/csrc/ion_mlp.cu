@@ -1,9 +1,11 @@
 // ion_mlp.cu -- learned surrogate of the channel rate functions (not in the paper).
 //
 // A small MLP, (V, [Ca]) -> 64 tanh -> 64 tanh -> 24 outputs, stands in for the gates'
-// rate functions: output 2g is x_inf of gate g, output 2g+1 is ln(tau) (the instantaneous
-// gates m_s, m_a have no tau; that output is masked out of the loss).  Inputs and outputs
-// are normalised (shift / scale kept with the weights).
+// rate functions: output 2g is logit(x_inf) of gate g (clipped to +-LOGIT_MAX), output 2g+1
+// is ln(tau) (the instantaneous gates m_s, m_a have no tau; that output is masked out of
+// the loss).  The logit keeps small steady states (m_inf^3 of the Na channels near rest)
+// accurate in relative terms; a first fit of x_inf itself made resting cells fire.  Inputs
+// and outputs are normalised (shift / scale kept with the weights).
 //
 // Training (ion_surrogate_train): samples V uniform in [v_lo, v_hi] and [Ca] log-uniform
 // are drawn on the device (splitmix64 in counter form, Steele-Lea-Flood 2014), labelled
@@ -37,6 +39,7 @@ constexpr int P_W1 = 0, P_B1 = P_W1 + MH * MI, P_W2 = P_B1 + MH, P_B2 = P_W2 + M
 constexpr int MB = 128;                                      // samples per CTA in training
 constexpr int HS = MH + 1;                                   // padded row stride of activation tiles
 constexpr float V_CENTER = -25.0f, V_HALF = 75.0f;
+constexpr float LOGIT_MAX = 15.0f;
 
 // ---- counter-based generator (splitmix64) --------------------------------------------
 __device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
@@ -58,12 +61,15 @@ __global__ void mlp_samples_kernel(int64_t n, uint64_t seed, float v_lo, float v
     ca[k] = (float)exp(lc_lo + (lc_hi - lc_lo) * sm64_uniform(sb, (uint64_t)k));
 }
 
-// raw targets of one (V, ca): x_inf and ln(tau) of every gate (0 for the instantaneous ones)
+// raw targets of one (V, ca): logit(x_inf) and ln(tau) of every gate (ln tau = 0 for the
+// instantaneous ones)
 __device__ __forceinline__ void exact_targets(float V, float ca, float *out) {
     const Rate g[NG] = {rate_r(V), rate_s(ca), rate_q(V), rate_k(V), rate_l(V), {minf_na(V), 0.0f},
                         rate_hs(V), rate_ns(V), rate_x(V), {minf_na(V), 0.0f}, rate_ha(V), rate_x(V)};
     for (int k = 0; k < NG; ++k) {
-        out[2 * k] = g[k].xinf;
+        const float x = fminf(fmaxf(g[k].xinf, 1e-30f), 1.0f);
+        const float lg = logf(x) - log1pf(-fminf(x, 1.0f - 1e-7f));
+        out[2 * k] = fminf(fmaxf(lg, -LOGIT_MAX), LOGIT_MAX);
         out[2 * k + 1] = g[k].inv_tau > 0.0f ? -logf(g[k].inv_tau) : 0.0f;
     }
 }
@@ -458,9 +464,12 @@ struct SurrArgs {
     const float *ic;    // gap currents of this step (NULL: none)
 };
 
+// x_inf = 1 / (1 + e^{-logit}), 1 / tau = e^{-ln tau}
+__device__ __forceinline__ float learned_xinf(const float *y, int gate) {
+    return rcp_approx(1.0f + ex2_approx(-y[2 * gate] * 1.4426950408889634f));
+}
 __device__ __forceinline__ Rate learned_rate(const float *y, int gate) {
-    const float xinf = fminf(fmaxf(y[2 * gate], 0.0f), 1.0f);
-    return Rate{xinf, ex2_approx(-y[2 * gate + 1] * 1.4426950408889634f)};   // 1/tau = e^{-ln tau}
+    return Rate{learned_xinf(y, gate), ex2_approx(-y[2 * gate + 1] * 1.4426950408889634f)};
 }
 
 __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
@@ -506,11 +515,11 @@ __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
     gr.q = learned_rate(yd, G_Q);
     gr.k = learned_rate(ysm, G_K);
     gr.l = learned_rate(ysm, G_L);
-    gr.ms = Rate{fminf(fmaxf(ysm[2 * G_MS], 0.0f), 1.0f), 0.0f};
+    gr.ms = Rate{learned_xinf(ysm, G_MS), 0.0f};
     gr.hs = learned_rate(ysm, G_HS);
     gr.ns = learned_rate(ysm, G_NS);
     gr.xs = learned_rate(ysm, G_XS);
-    gr.ma = Rate{fminf(fmaxf(yax[2 * G_MA], 0.0f), 1.0f), 0.0f};
+    gr.ma = Rate{learned_xinf(yax, G_MA), 0.0f};
     gr.ha = learned_rate(yax, G_HA);
     gr.xa = learned_rate(yax, G_XA);
     const float ic = a.ic != nullptr ? a.ic[i] : 0.0f;

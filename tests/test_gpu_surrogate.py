@@ -25,7 +25,7 @@ def cuda():
 
 @pytest.fixture(scope="module")
 def trained(cuda):
-    w, loss = ion.ion_surrogate_train(n_samples=1 << 18, epochs=12, batch=2048, lr=2e-3, seed=7, v_lo=-100.0,
+    w, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=30, batch=2048, lr=2e-3, seed=7, v_lo=-100.0,
                                       v_hi=50.0, ca_lo=CA_RANGE[0], ca_hi=CA_RANGE[1])
     print(f"surrogate training: final normalised loss {loss:.3e}")
     return w, loss
@@ -74,11 +74,12 @@ def test_trained_surrogate_fits_the_rate_functions(trained, O):
     ca = np.exp(rng.uniform(np.log(CA_RANGE[0]), np.log(CA_RANGE[1]), 4000)).astype(np.float32)
     got = ion.ion_surrogate_eval(w, V, ca)
     ref, mask = mlp.gate_targets(V, ca)
-    xinf_err = np.abs(got[:, 0::2] - ref[:, 0::2])
+    xinf_err = np.abs(mlp.sigmoid(got[:, 0::2]) - mlp.sigmoid(ref[:, 0::2]))
+    logit_err = np.abs(got[:, 0::2] - ref[:, 0::2])
     lntau_err = np.abs(got[:, 1::2] - ref[:, 1::2])[:, mask[1::2] > 0]
-    print(f"x_inf |err| mean {xinf_err.mean():.2e} max {xinf_err.max():.2e}; "
-          f"ln tau |err| mean {lntau_err.mean():.2e} max {lntau_err.max():.2e}")
-    assert xinf_err.mean() < 0.01 and xinf_err.max() < 0.1
+    print(f"x_inf |err| mean {xinf_err.mean():.2e} max {xinf_err.max():.2e}; logit |err| mean "
+          f"{logit_err.mean():.2e}; ln tau |err| mean {lntau_err.mean():.2e} max {lntau_err.max():.2e}")
+    assert xinf_err.mean() < 5e-3 and xinf_err.max() < 0.1
     assert lntau_err.mean() < 0.05
 
 

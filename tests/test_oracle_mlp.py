@@ -33,7 +33,9 @@ def test_mlp_gradients_match_finite_differences(O):
 def test_targets_follow_rate_functions(O):
     out, mask = mlp.gate_targets([-30.0, -80.0], [1.0, 1.0])
     G = {g: i for i, g in enumerate(O.GATES)}
-    assert out[0, 2 * G["m_s"]] == pytest.approx(0.5)            # m_inf(-30) = 1/2
-    assert out[1, 2 * G["q"]] == pytest.approx(0.5)              # q_inf(-80) = 1/2
+    assert out[0, 2 * G["m_s"]] == pytest.approx(0.0, abs=1e-12)   # logit(m_inf(-30)) = logit(1/2)
+    assert out[1, 2 * G["q"]] == pytest.approx(0.0, abs=1e-12)     # q_inf(-80) = 1/2
+    assert mlp.sigmoid(mlp.gate_targets([-47.0], [1.0])[0][0, 2 * G["h_s"]]) == pytest.approx(
+        O.rates(-47.0, 1.0)[0][G["h_s"]], rel=1e-12)
     assert out[0, 2 * G["k"] + 1] == 0.0                          # ln(tau_k) = ln 1
     assert mask[2 * G["m_s"] + 1] == 0 and mask[2 * G["m_a"] + 1] == 0 and mask.sum() == 22
