@@ -6,7 +6,9 @@ bench step simulates 200 ms = 4000 time steps of 50 us from the same initial sta
 Metric: cell-timesteps/s (and gap-junction pair evaluations/s, N^2 per time step).
 
 `--workload` selects another configuration for a secondary line (c1: 64 dense cells for
-1 s; c3_k10 / c3_k100 / c3_k1000: 65 536 cells with random symmetric CSR connectivity).
+1 s; c3_k10 / c3_k100 / c3_k1000: 65 536 cells with random symmetric CSR connectivity;
+c4: 256 uneven networks in one batch; c5: the k = 100 network for 1 s with the learned
+rate-function surrogate against the exact FP32 method).
 `--impl reference` times the FP64 CPU oracle instead (a bounded sample, all host cores).
 Prints one JSON line.
 """
@@ -35,6 +37,7 @@ WORKLOADS = {
     "c3_k100": dict(name="c3_csr_65536_k100_200ms", cfg="c3", k=100, steps=4000),
     "c3_k1000": dict(name="c3_csr_65536_k1000_200ms", cfg="c3", k=1000, steps=4000),
     "c4": dict(name="c4_batch_256_nets_logU32-4096_half_dense_100ms", cfg="c4", steps=2000),
+    "c5": dict(name="c5_surrogate_csr_65536_k100_1s", cfg="c3", k=100, steps=20000),
 }
 
 
@@ -200,6 +203,14 @@ def main():
     S0 = ion.ion_default_state(n)
     S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
     tune_table = None
+    surrogate = None
+    surrogate_info = {}
+    if key == "c5":
+        t0 = time.perf_counter()
+        surrogate, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=30, batch=2048, lr=2e-3, seed=7,
+                                                  v_lo=-100.0, v_hi=50.0, ca_lo=1.36, ca_hi=13.5, stream=stream)
+        surrogate_info = {"train_seconds": time.perf_counter() - t0, "train_samples": 1 << 20, "epochs": 30,
+                          "final_loss_normalised": loss}
     stream = torch.cuda.current_stream().cuda_stream
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
@@ -215,6 +226,8 @@ def main():
             tune_table = ion.ion_autotune(sim.h, 20)     # project-written autotuner: time the tile shapes
             return sim
         kw = dict(g=cfg["g"]) if dense else dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
+        if flags & ion.FLAG_SURROGATE:
+            kw["surrogate"] = surrogate
         sim = ion.Simulation(n, ion.DENSE_UNIFORM if dense else ion.CSR, init_state=S0, stream=stream,
                              graph_steps=100, flags=flags, **kw)
         if cfg.get("pulses") is not None:
@@ -261,11 +274,26 @@ def main():
         cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
     if args.variant != "auto":
         cand = [c for c in cand if c[0] == args.variant]
+    if key == "c5":
+        cand = [("exact", ion.FLAG_KAHAN), ("surrogate", ion.FLAG_KAHAN | ion.FLAG_SURROGATE)]
     variants = {}
     for name, flags in cand:
         sim_v, ms_v, l_v, ck_v = measure(flags)
         variants[name] = dict(sim=sim_v, ms=ms_v, launches=l_v, clocks=ck_v)
     best = min(variants, key=lambda k: variants[k]["ms"])
+    if key == "c5":   # the line reports the surrogate; the exact method is its comparison
+        best = "surrogate"
+        finals = {}
+        for name in ("exact", "surrogate"):
+            v = variants[name]["sim"]
+            reset(v)
+            v.step(sim_steps)
+            finals[name] = v.state()
+        dv = np.abs(finals["exact"][:3] - finals["surrogate"][:3])
+        surrogate_info.update({
+            "exact_cell_timesteps_per_s": n * sim_steps * args.steps / (variants["exact"]["ms"] * 1e-3),
+            "speedup_vs_exact": variants["exact"]["ms"] / variants["surrogate"]["ms"],
+            "final_state_max_abs_dV_mV": float(dv.max()), "final_state_mean_abs_dV_mV": float(dv.mean())})
     sim, ms, launches, ck = (variants[best][k] for k in ("sim", "ms", "launches", "clocks"))
     for k, v in variants.items():
         if k != best:
@@ -295,6 +323,20 @@ def main():
                 "peak_source": "measured SFU ex2 rate (ion_probe_peak) in the same process",
                 "ffma_peak_per_s": ion.ion_probe_peak(1, 4096, stream), "us_per_timestep": per_step_s * 1e6}
         extra = {"pair_evals_per_s": value * n}
+    elif key == "c5":
+        # the surrogate's cell kernel: 3 MLP evaluations per cell on the tensor cores
+        flops = 3 * 2 * (2 * 64 + 64 * 64 + 64 * 24)
+        achieved = n * flops / per_step_s / 1e12
+        peak = 1887.2
+        try:
+            peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+        except (OSError, KeyError, ValueError):
+            pass
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "surrogate_cell_kernel (+ csr_step_kernel for the gap currents)",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst)", "us_per_timestep": per_step_s * 1e6,
+                "mlp_flop_per_cell_step": flops}
+        extra = {"surrogate": surrogate_info}
     else:
         # HBM: per time step the CSR (8 B per edge + 4 B per row), the cell state
         # (15 words read + 18 written) and the pulse offsets (8 B per cell)
