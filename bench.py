@@ -54,6 +54,22 @@ def parse():
     return ap.parse_args()
 
 
+def replica_reduce(ms_local: float, cells_local: float, pg=None):
+    """Whole-job figures of N independent replicas: the slowest rank's time bounds the job
+    and the cells of all ranks count (weak scaling: every rank runs a full workload).
+    Returns (value = total cells / max time, max time in ms).  pg: torch.distributed or None."""
+    ms, cells = float(ms_local), float(cells_local)
+    if pg is not None:
+        import torch
+        dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        c = torch.tensor([cells], dtype=torch.float64, device=dev)
+        pg.all_reduce(c, op=pg.ReduceOp.SUM)
+        ms, cells = float(t.item()), float(c.item())
+    return cells / (ms * 1e-3), ms
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
@@ -203,6 +219,8 @@ def main():
     S0 = ion.ion_default_state(n)
     S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
     tune_table = None
+    stream = torch.cuda.current_stream().cuda_stream
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     surrogate = None
     surrogate_info = {}
     if key == "c5":
@@ -211,8 +229,6 @@ def main():
                                                   v_lo=-100.0, v_hi=50.0, ca_lo=1.36, ca_hi=13.5, stream=stream)
         surrogate_info = {"train_seconds": time.perf_counter() - t0, "train_samples": 1 << 20, "epochs": 30,
                           "final_loss_normalised": loss}
-    stream = torch.cuda.current_stream().cuda_stream
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def make_sim(flags):
         nonlocal tune_table
@@ -262,10 +278,6 @@ def main():
         ck = clocks.stop()
         launches = sim.launches - launches0
         ms = sum(a.elapsed_time(b) for a, b in ev)
-        if pg:
-            t = torch.tensor([ms], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
         sim.sync()                                      # the run stayed finite
         return sim, ms, launches, ck
 
@@ -300,7 +312,7 @@ def main():
             v["sim"].close()
 
     cell_steps = n * sim_steps * args.steps * world
-    value = cell_steps / (ms * 1e-3)
+    value, ms = replica_reduce(ms, n * sim_steps * args.steps, pg)   # slowest rank, cells of all ranks
     per_step_s = ms * 1e-3 / (sim_steps * args.steps)
     if batch:
         # one ex2 per dense pair and per CSR edge; the SFU rate bounds the mix
@@ -384,12 +396,9 @@ def main():
             out_pin.numpy()[:] = ion.ion_read_state(sim.h, n)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([e2e_s], device="cuda")
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_value, _ = replica_reduce(e2e_s * 1e3, n * sim_steps * e2e_steps, pg)
         if rank == 0:
-            line["e2e"] = {"value": n * sim_steps * e2e_steps * world / e2e_s, "unit": METRIC,
+            line["e2e"] = {"value": e2e_value, "unit": METRIC,
                            "h2d_bytes_per_step": int(S0.nbytes), "d2h_bytes_per_step": int(S0.nbytes)}
             cpu = cpu_baseline(key, reference_sample_steps(key) if key != "c2" else 3)
             line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
