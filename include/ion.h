@@ -88,12 +88,16 @@ enum ion_mem { ION_HOST = 0, ION_DEVICE = 1 };
 enum ion_flag {
     ION_FLAG_KAHAN = 1u << 0,      /* compensated dense gap-junction sums (default on)     */
     ION_FLAG_PERSISTENT = 1u << 1, /* dense: one cooperative launch per ion_step call, state in
-                                      registers, bounded grid barrier per step (if every CTA
-                                      fits on the GPU at once; else per-step launches)        */
+                                      registers, bounded grid barriers per step (if every CTA
+                                      fits on the GPU at once; else per-step launches).  With
+                                      several CTAs each unordered pair is evaluated once
+                                      (I_ij = -I_ji) unless ION_FLAG_NO_HALF is set           */
     ION_FLAG_SURROGATE = 1u << 2,  /* MLP surrogate for the channel rate functions         */
     ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
     ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
-    ION_FLAG_SPLIT = 1u << 5       /* separate gap-junction and cell-update kernels         */
+    ION_FLAG_SPLIT = 1u << 5,      /* separate gap-junction and cell-update kernels         */
+    ION_FLAG_NO_HALF = 1u << 6     /* persistent dense: evaluate every ordered pair instead of
+                                      each unordered pair once (the default for >= 2 CTAs)  */
 };
 
 typedef struct {

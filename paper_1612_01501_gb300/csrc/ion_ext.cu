@@ -10,6 +10,37 @@
 using namespace ion;
 
 // ---- persistent dense launches ----------------------------------------------------------
+// Multi-CTA networks use the half-work kernel (each unordered pair once, two barriers per
+// step); one-CTA networks the full-work kernel with V_dend kept in shared memory.
+static ion_status half_run(ion_sim *s, int64_t n_steps, const float *iapp) {
+    (void)iapp;
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 22);   // 2 * chunk * grid < 2^32
+        HalfArgs a{};
+        a.c = ion_step_common(s, 0, nullptr);
+        a.g = s->g;
+        a.n_steps = chunk;
+        a.rows = (s->persist_W / s->persist_GJ) * s->persist_R;
+        a.bar_count = s->d_bar;
+        a.abort_flag = s->d_bar + 1;
+        a.timeout_ns = s->barrier_timeout_ns;
+        a.debug_delay_ns = s->debug_delay_ns;
+        a.colsum = s->d_half;
+        a.colsum_stride = s->half_stride;
+        a.usum = s->d_half + (int64_t)s->half_grid * s->half_stride;
+        cudaError_t e = cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(uint32_t), s->st);
+        if (e == cudaSuccess)
+            e = launch_dense_half(a, s->persist_R, s->persist_W, s->persist_GJ, s->half_grid, true, nullptr, s->st);
+        s->launches++;
+        if (e == cudaSuccess) e = launch_advance(s->d_t, chunk, s->st);
+        s->launches++;
+        if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "persistent launch: %s", cudaGetErrorString(e));
+        done += chunk;
+    }
+    return ION_OK;
+}
+
 static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
     (void)iapp;
     int64_t done = 0;
@@ -72,9 +103,28 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
             if (cudaMalloc(&s->d_bar, 2 * sizeof(uint32_t)) != cudaSuccess)
                 return ion_fail(nullptr, ION_ERR_OOM, "persistent: barrier allocation failed");
             s->run_override = persist_run;
+            // several CTAs: the half-work kernel, if its shape and grid fit
+            const int rows = (s->persist_W / s->persist_GJ) * s->persist_R;
+            const int grid = (s->n + rows - 1) / rows;
+            if (grid >= 2 && s->persist_R <= 4 && s->persist_W <= 28 && !(s->flags & ION_FLAG_NO_HALF)) {
+                HalfArgs probe{};
+                probe.rows = rows;
+                int fits = 0;
+                if (launch_dense_half(probe, s->persist_R, s->persist_W, s->persist_GJ, grid, false, &fits, s->st) ==
+                        cudaSuccess &&
+                    fits) {
+                    s->half_grid = grid;
+                    s->half_stride = half_colsum_stride(grid, rows);
+                    if (cudaMalloc(&s->d_half, ((size_t)grid * s->half_stride + grid) * sizeof(float)) != cudaSuccess)
+                        return ion_fail(nullptr, ION_ERR_OOM, "persistent: column-sum buffer allocation failed");
+                    s->run_override = half_run;
+                }
+            }
             s->extra_free = [](ion_sim *q) {
                 cudaFree(q->d_bar);
+                cudaFree(q->d_half);
                 q->d_bar = nullptr;
+                q->d_half = nullptr;
             };
         }
     }

@@ -87,6 +87,19 @@ struct PersistArgs {
     uint64_t timeout_ns;  // bound on one grid-barrier wait
     int64_t debug_delay_ns;  // test hook: the last CTA sleeps this long before its first step
 };
+struct HalfArgs {
+    StepCommon c;          // k_off unused: the launch runs steps *t_dev .. *t_dev + n_steps - 1
+    float g;
+    int32_t n_steps;
+    int32_t rows;          // rows per CTA (the block size b)
+    uint32_t *bar_count;   // grid-barrier arrivals (zeroed before the launch)
+    uint32_t *abort_flag;
+    uint64_t timeout_ns;
+    int64_t debug_delay_ns;
+    float *colsum;         // [grid][colsum_stride] column sums of each CTA's tile (L2-resident)
+    int32_t colsum_stride;
+    float *usum;           // [grid] sum of u over each CTA's own rows
+};
 struct CellArgs {
     StepCommon c;
     const float *ic;      // NULL: no gap current
@@ -110,6 +123,9 @@ cudaError_t launch_default_state(const ModelF &P, float V0, float ca0, float gca
 cudaError_t prepare_dense_step(int rows_per_warp, int warps, int col_splits, int n_pad);
 cudaError_t persist_dense(const PersistArgs &a, int rows_per_warp, int warps, int col_splits, int *grid_out,
                           bool launch, cudaStream_t st);
+cudaError_t launch_dense_half(const HalfArgs &a, int rows_per_warp, int warps, int col_splits, int grid,
+                              bool launch, int *ok_out, cudaStream_t st);
+int half_colsum_stride(int grid, int rows_per_cta);
 int dense_max_threads(int rows_per_warp);     // thread limit of the step kernel
 int persist_max_threads(int rows_per_warp);   // thread limit of the persistent kernel
 

@@ -51,6 +51,8 @@ struct ion_sim {
     int64_t debug_delay_ns = 0;
     uint32_t *d_bar = nullptr;      // grid barrier counter + abort word (persistent launches)
     int persist_R = 0, persist_W = 0, persist_GJ = 1;
+    float *d_half = nullptr;        // half-work persistent kernel: column sums + per-CTA sums of u
+    int half_grid = 0, half_stride = 0;
     int device = 0, sms = 1;
     int dense_R = 1, dense_W = 4, dense_GJ = 1, csr_SW = 8, csr_rows = 256;
     int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk

@@ -31,13 +31,44 @@ def _run(n, g, S0, steps, flags, pulses=None, chunks=1, **kw):
         return sim.state(), sim.launches
 
 
-def test_persistent_multi_cta_bitwise_equals_step_launches(cuda, O):
+def test_persistent_full_work_bitwise_equals_step_launches(cuda, O):
     cfg = inputs.config("c2")
     S0 = initial_state(O, cfg)
     a, la = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN, chunks=3)
-    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT, chunks=3)
+    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_NO_HALF, chunks=3)
     np.testing.assert_array_equal(a, b)
     assert lb < la / 10        # one launch (+ one counter advance) per ion_step call
+
+
+def test_persistent_half_work_matches_step_launches(cuda, O):
+    """Each unordered pair evaluated once: a different summation order, so close, not equal."""
+    cfg = inputs.config("c2")
+    S0 = initial_state(O, cfg)
+    a, _ = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN, chunks=3)
+    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT, chunks=3)
+    assert np.abs(a[:3] - b[:3]).max() <= 1e-3
+    assert lb == 6
+
+
+@pytest.mark.parametrize("n,tune", [(8192, None), (4096, None), (1000, dict(dense_rows_per_warp=2, dense_warps=8,
+                                                                           dense_col_splits=1)),
+                                    (3001, dict(dense_rows_per_warp=4, dense_warps=16, dense_col_splits=2))])
+def test_half_work_one_step_matches_oracle(cuda, O, n, tune):
+    """One step of the half-work kernel (odd and even grids, one or two column splits)
+    from an identical state, against the FP64 oracle (per-step bound 1e-5)."""
+    from helpers import STEP_RTOL, step_rel_err, sum_abs_dv
+    g = inputs.junction_weight(0.04, n)
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 77))
+    S0 = initial_state(O, cfg)
+    Sw, _ = O.run(S0.astype(np.float64), 20, kind=O.DENSE, g=g, threads=max(1, O.max_threads()))
+    Sw32 = Sw.astype(np.float32)
+    ref, _ = O.run(Sw32.astype(np.float64), 1, kind=O.DENSE, g=g, threads=max(1, O.max_threads()))
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=g, init_state=Sw32, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
+                        tune=tune) as sim:
+        sim.step(1)
+        got = sim.state()
+    err = step_rel_err(got, ref, g * sum_abs_dv(Sw32[0]))
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
 
 
 @pytest.mark.parametrize("n", [64, 100, 1000])
@@ -83,3 +114,14 @@ def test_grid_barrier_timeout_is_reported_not_hung(cuda, O):
     with ion.Simulation(n, ion.DENSE_UNIFORM, g=0.01, init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT) as s2:
         s2.step(5)
         s2.sync()
+
+
+def test_half_work_barrier_timeout_is_reported(cuda, O):
+    n = 4096        # several CTAs: the half-work kernel, two bounded barriers per step
+    S0 = O.default_state(n).astype(np.float32)
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=0.001, init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
+                        barrier_timeout_ns=1_000_000, debug_delay_ns=200_000_000) as sim:
+        sim.step(5)
+        with pytest.raises(ion.IonError) as ei:
+            sim.sync()
+        assert ei.value.status == ion.ERR_TIMEOUT
