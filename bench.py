@@ -8,7 +8,8 @@ Metric: cell-timesteps/s (and gap-junction pair evaluations/s, N^2 per time step
 `--workload` selects another configuration for a secondary line (c1: 64 dense cells for
 1 s; c3_k10 / c3_k100 / c3_k1000: 65 536 cells with random symmetric CSR connectivity;
 c4: 256 uneven networks in one batch; c5: the k = 100 network for 1 s with the learned
-rate-function surrogate against the exact FP32 method).
+rate-function surrogate against the exact FP32 method; k3: the cell update alone on 2^22
+uncoupled cells, with a sweep of sizes from 2^16).
 `--impl reference` times the FP64 CPU oracle instead (a bounded sample, all host cores).
 Prints one JSON line.
 """
@@ -38,7 +39,9 @@ WORKLOADS = {
     "c3_k1000": dict(name="c3_csr_65536_k1000_200ms", cfg="c3", k=1000, steps=4000),
     "c4": dict(name="c4_batch_256_nets_logU32-4096_half_dense_100ms", cfg="c4", steps=2000),
     "c5": dict(name="c5_surrogate_csr_65536_k100_1s", cfg="c3", k=100, steps=20000),
+    "k3": dict(name="k3_cell_update_ngj_4194304_20ms", cfg="k3", n=1 << 22, steps=400),
 }
+K3_SWEEP = (1 << 16, 1 << 18, 1 << 20, 1 << 22)
 
 
 def parse():
@@ -49,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--sim-steps", type=int, default=0, help="time steps per bench step (0: the workload's)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "graph", "persistent"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "graph", "persistent", "persistent_full"])
     ap.add_argument("--no-extra", action="store_true", help="skip the CPU baseline and the e2e leg")
     return ap.parse_args()
 
@@ -116,6 +119,112 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def hbm_peak():
+    """Measured copy bandwidth of this machine's GB300 (GB/s), else the earlier measurement."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6792.4
+
+
+def k3_sweep(ion, torch, stream, flush, sim_steps, warmup, known, peak):
+    """Cell update alone (uncoupled cells) at each size of K3_SWEEP: us per time step and
+    GB/s of algorithmic bytes (132 B of state + the pulse table per cell).  Sizes already
+    timed are passed in `known` ({n: seconds per time step})."""
+    from paper_1612_01501_gb300 import inputs
+    out = {}
+    for n in K3_SWEEP:
+        cfg = inputs.config("k3", n=n)
+        per = known.get(n)
+        if per is None:
+            S0 = ion.ion_default_state(n)
+            S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
+            with ion.Simulation(n, ion.NO_GJ, init_state=S0, stream=stream, graph_steps=100) as sim:
+                sim.set_input(cfg["pulses"])
+                for _ in range(warmup):
+                    sim.step(sim_steps)
+                reps, ms = 3, 0.0
+                for r in range(reps):
+                    flush.fill_(float(r))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    sim.step(sim_steps)
+                    b.record()
+                    torch.cuda.synchronize()
+                    ms += a.elapsed_time(b)
+                sim.sync()
+            per = ms * 1e-3 / (reps * sim_steps)
+        by = 132 * n + 4 * (n + 1) + 20 * len(cfg["pulses"][0])
+        out[str(n)] = {"us_per_timestep": per * 1e6, "gb_per_s": by / per / 1e9, "frac": by / per / 1e9 / peak,
+                       "state_mb": 80 * n / 1e6}
+    return out
+
+
+class SpikeLog:
+    """Spike times of every cell from streamed V_axon samples: an upward crossing of 0 mV
+    (the first sample at or above it), re-armed once V_axon falls below -30 mV."""
+
+    def __init__(self, n):
+        self.armed = np.ones(n, bool)
+        self.t = 0
+        self.cells, self.steps = [], []
+
+    def feed(self, trace):
+        for row in trace:
+            fire = self.armed & (row >= 0.0)
+            idx = np.flatnonzero(fire)
+            if len(idx):
+                self.cells.append(idx)
+                self.steps.append(np.full(len(idx), self.t, np.int64))
+            self.armed = (self.armed & ~fire) | (~self.armed & (row < -30.0))
+            self.t += 1
+
+    def sorted(self):
+        c = np.concatenate(self.cells) if self.cells else np.zeros(0, np.int64)
+        t = np.concatenate(self.steps) if self.steps else np.zeros(0, np.int64)
+        o = np.lexsort((t, c))
+        return c[o], t[o]
+
+
+def compare_runs(ion, sim_a, sim_b, reset, n, steps, chunk=2000):
+    """Run two handles side by side from the same state with V_axon traced every step;
+    return the trace error and the spike-time agreement of b against a.  Spikes are
+    matched in order within each cell whose spike counts agree."""
+    logs = [SpikeLog(n), SpikeLog(n)]
+    sq, mx, cnt = 0.0, 0.0, 0
+    for sim in (sim_a, sim_b):
+        reset(sim)
+        ion.ion_set_trace(sim.h, 1, chunk)
+    done = 0
+    while done < steps:
+        c = min(chunk, steps - done)
+        tr = []
+        for sim, log in zip((sim_a, sim_b), logs):
+            sim.step(c)
+            t = ion.ion_read_trace(sim.h, n, c)
+            log.feed(t)
+            tr.append(t)
+        d = tr[0].astype(np.float64) - tr[1]
+        sq += float((d * d).sum())
+        mx = max(mx, float(np.abs(d).max()))
+        cnt += d.size
+        done += c
+    for sim in (sim_a, sim_b):
+        ion.ion_set_trace(sim.h, 0, 0)
+    (ca, ta), (cb, tb) = logs[0].sorted(), logs[1].sorted()
+    na, nb = np.bincount(ca, minlength=n), np.bincount(cb, minlength=n)
+    same = na == nb
+    da = np.abs(ta[same[ca]] - tb[same[cb]])
+    return {"v_axon_rms_mV": (sq / max(cnt, 1)) ** 0.5, "v_axon_max_abs_mV": mx,
+            "spikes_exact": int(len(ca)), "spikes_surrogate": int(len(cb)),
+            "spiking_cells_exact": int((na > 0).sum()),
+            "cells_same_spike_count_frac": float(same.mean()),
+            "spikes_within_1_step_frac": float((da <= 1).sum() / max(len(ca), 1)),
+            "matched_max_abs_dstep": int(da.max()) if len(da) else 0,
+            "matched_mean_abs_dstep": float(da.mean()) if len(da) else 0.0,
+            "compared_steps": int(steps)}
+
+
 def load_workload(key):
     """Input bundle of a workload (seeded, synthetic) as the oracle and the GPU see it."""
     from paper_1612_01501_gb300 import inputs
@@ -129,7 +238,7 @@ def load_workload(key):
             off += b["n"]
         pul = (np.concatenate(cells).astype(np.int32), np.concatenate(beg), np.concatenate(end), np.concatenate(amp))
         return dict(n=off, kind="batch", nets=nets, jitter=np.concatenate([b["jitter"] for b in nets]), pulses=pul)
-    return inputs.config(w["cfg"], k=w.get("k"))
+    return inputs.config(w["cfg"], k=w.get("k"), n=w.get("n"))
 
 
 def cpu_baseline(key, sample_steps):
@@ -143,7 +252,7 @@ def cpu_baseline(key, sample_steps):
         S = O.default_state(b["n"])
         S[O.F["V_dend"]] += b["jitter"]
         S = S.astype(np.float32).astype(np.float64)
-        kind = O.DENSE if b["kind"] == "dense" else O.CSR
+        kind = {"dense": O.DENSE, "csr": O.CSR, "ngj": O.NOGJ}[b["kind"]]
         kw = dict(kind=kind, g=b.get("g", 0.0), row_ptr=b.get("row_ptr"), col=b.get("col"),
                   w=None if b.get("w") is None else b["w"].astype(np.float64), threads=threads)
         runs.append((S, kw))
@@ -159,7 +268,7 @@ def cpu_baseline(key, sample_steps):
 
 
 def reference_sample_steps(key):
-    return {"c2": 8, "c1": 2000, "c4": 3}.get(key, 20)
+    return {"c2": 8, "c1": 2000, "c4": 3, "k3": 3}.get(key, 20)
 
 
 def run_reference(args, rank):
@@ -216,6 +325,7 @@ def main():
     n = cfg["n"]
     dense = cfg["kind"] == "dense"
     batch = cfg["kind"] == "batch"
+    ngj = cfg["kind"] == "ngj"
     S0 = ion.ion_default_state(n)
     S0[0] = (S0[0].astype(np.float64) + cfg["jitter"]).astype(np.float32)
     tune_table = None
@@ -241,11 +351,15 @@ def main():
             sim.set_input(cfg["pulses"])
             tune_table = ion.ion_autotune(sim.h, 20)     # project-written autotuner: time the tile shapes
             return sim
-        kw = dict(g=cfg["g"]) if dense else dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
+        if ngj:
+            kind, kw = ion.NO_GJ, {}
+        elif dense:
+            kind, kw = ion.DENSE_UNIFORM, dict(g=cfg["g"])
+        else:
+            kind, kw = ion.CSR, dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
         if flags & ion.FLAG_SURROGATE:
             kw["surrogate"] = surrogate
-        sim = ion.Simulation(n, ion.DENSE_UNIFORM if dense else ion.CSR, init_state=S0, stream=stream,
-                             graph_steps=100, flags=flags, **kw)
+        sim = ion.Simulation(n, kind, init_state=S0, stream=stream, graph_steps=100, flags=flags, **kw)
         if cfg.get("pulses") is not None:
             sim.set_input(cfg["pulses"])
         return sim
@@ -284,6 +398,8 @@ def main():
     cand = [("graph", ion.FLAG_KAHAN)]
     if dense:
         cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
+        if n > 144:   # multi-CTA networks: the full pass as well as the half-work pass
+            cand.append(("persistent_full", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_NO_HALF))
     if args.variant != "auto":
         cand = [c for c in cand if c[0] == args.variant]
     if key == "c5":
@@ -295,17 +411,23 @@ def main():
     best = min(variants, key=lambda k: variants[k]["ms"])
     if key == "c5":   # the line reports the surrogate; the exact method is its comparison
         best = "surrogate"
-        finals = {}
-        for name in ("exact", "surrogate"):
-            v = variants[name]["sim"]
-            reset(v)
-            v.step(sim_steps)
-            finals[name] = v.state()
-        dv = np.abs(finals["exact"][:3] - finals["surrogate"][:3])
         surrogate_info.update({
             "exact_cell_timesteps_per_s": n * sim_steps * args.steps / (variants["exact"]["ms"] * 1e-3),
-            "speedup_vs_exact": variants["exact"]["ms"] / variants["surrogate"]["ms"],
-            "final_state_max_abs_dV_mV": float(dv.max()), "final_state_mean_abs_dV_mV": float(dv.mean())})
+            "speedup_vs_exact": variants["exact"]["ms"] / variants["surrogate"]["ms"]})
+        surrogate_info.update(compare_runs(ion, variants["exact"]["sim"], variants["surrogate"]["sim"], reset,
+                                           n, sim_steps))
+        # the workload's pulse reaches 20 % of the cells and drains into their neighbours
+        # (no cell fires); the spike times are compared on the same network with every
+        # cell pulsed at 50-60 ms and 500-510 ms
+        from paper_1612_01501_gb300 import inputs
+        spiking = inputs.config("c3_spiking", k=wl["k"])
+        for name in ("exact", "surrogate"):
+            variants[name]["sim"].set_input(spiking["pulses"])
+        surrogate_info["spiking_comparison"] = dict(
+            workload="c3_spiking_csr_65536_k100_1s (every cell pulsed at 50-60 and 500-510 ms)",
+            **compare_runs(ion, variants["exact"]["sim"], variants["surrogate"]["sim"], reset, n, sim_steps))
+        for name in ("exact", "surrogate"):
+            variants[name]["sim"].set_input(cfg["pulses"])
     sim, ms, launches, ck = (variants[best][k] for k in ("sim", "ms", "launches", "clocks"))
     for k, v in variants.items():
         if k != best:
@@ -327,14 +449,30 @@ def main():
                  "edges_per_s": sum(len(b["col"]) for b in cfg["nets"] if b["kind"] == "csr") / per_step_s,
                  "autotuned": tune_table, "n_networks": len(cfg["nets"])}
     elif dense:
-        # SFU-bound: one ex2 per pair evaluation (N^2 per time step)
+        # SFU-bound: one ex2 per pair evaluation (N^2 per time step); the half-work kernel
+        # evaluates each unordered pair once (N^2 / 2 ex2 per time step)
+        half = best == "persistent" and n > 144
+        ex2_step = n * n / 2 if half else n * n
         peak = ion.ion_probe_peak(0, 4096, stream)
-        achieved = n * n / per_step_s
+        achieved = ex2_step / per_step_s
         roof = {"bound": "alu", "unit": "ex2/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None, "kernel": "dense_persist_kernel" if best == "persistent" else "dense_step_kernel",
+                "traffic": None, "kernel": {"persistent": "dense_half_kernel" if n > 144 else "dense_persist_kernel",
+                           "persistent_full": "dense_persist_kernel"}.get(best, "dense_step_kernel"),
                 "peak_source": "measured SFU ex2 rate (ion_probe_peak) in the same process",
-                "ffma_peak_per_s": ion.ion_probe_peak(1, 4096, stream), "us_per_timestep": per_step_s * 1e6}
+                "ffma_peak_per_s": ion.ion_probe_peak(1, 4096, stream), "us_per_timestep": per_step_s * 1e6,
+                "ex2_per_timestep": ex2_step}
         extra = {"pair_evals_per_s": value * n}
+    elif ngj:
+        # HBM: per time step the cell state (15 words read + 18 written) and the pulse
+        # table (4 B offset per cell + 20 B per pulse, 20 % of cells pulsed)
+        bytes_step = 132 * n + 4 * (n + 1) + 20 * len(cfg["pulses"][0])
+        achieved = bytes_step / per_step_s / 1e9
+        peak = hbm_peak()
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "cell_step_kernel", "algorithmic_bytes_per_timestep": bytes_step,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6,
+                "note": "state (%.0f MB) larger than L2 (129 MB)" % (80 * n / 1e6)}
+        extra = {"sweep": k3_sweep(ion, torch, stream, flush, sim_steps, args.warmup, {n: per_step_s}, peak)}
     elif key == "c5":
         # the surrogate's cell kernel: 3 MLP evaluations per cell on the tensor cores
         flops = 3 * 2 * (2 * 64 + 64 * 64 + 64 * 24)
@@ -350,20 +488,21 @@ def main():
                 "mlp_flop_per_cell_step": flops}
         extra = {"surrogate": surrogate_info}
     else:
-        # HBM: per time step the CSR (8 B per edge + 4 B per row), the cell state
-        # (15 words read + 18 written) and the pulse offsets (8 B per cell)
+        # HBM: per time step the CSR as the handle stores it (index + weight bytes per edge,
+        # 4 B per row pointer, 4 B per row and interior chunk boundary when staged), the cell
+        # state (15 words read + 18 written) and the pulse table (8 B per cell on average)
         nnz = len(cfg["col"])
-        bytes_step = 8 * nnz + 4 * (n + 1) + 132 * n + 8 * n
+        lay = ion.ion_csr_layout(sim.h)
+        n_chunks = (n + 32767) // 32768 if lay["staged"] else 1
+        bytes_step = ((lay["index_bytes"] + lay["weight_bytes"]) * nnz + 4 * (n + 1) + 4 * n * (n_chunks - 1)
+                      + 132 * n + 8 * n)
         achieved = bytes_step / per_step_s / 1e9
-        peak = 6792.4
-        try:
-            peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
-        except (OSError, KeyError, ValueError):
-            pass
+        peak = hbm_peak()
         roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": None, "kernel": "csr_step_kernel", "algorithmic_bytes_per_timestep": bytes_step,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6,
-                "note": "working set fits in L2 (129 MB)" if bytes_step < 100e6 else "streams from HBM"}
+                "note": "working set fits in L2 (129 MB)" if bytes_step < 100e6 else "streams from HBM",
+                "csr_layout": lay}
         extra = {"edges_per_s": value / n * nnz, "nnz": nnz}
 
     line = None

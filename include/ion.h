@@ -96,8 +96,10 @@ enum ion_flag {
     ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
     ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
     ION_FLAG_SPLIT = 1u << 5,      /* separate gap-junction and cell-update kernels         */
-    ION_FLAG_NO_HALF = 1u << 6     /* persistent dense: evaluate every ordered pair instead of
+    ION_FLAG_NO_HALF = 1u << 6,    /* persistent dense: evaluate every ordered pair instead of
                                       each unordered pair once (the default for >= 2 CTAs)  */
+    ION_FLAG_CSR_AS_GIVEN = 1u << 7 /* CSR: keep 32-bit columns and per-edge weights even when
+                                      a compact layout applies (see ion_csr_layout)         */
 };
 
 typedef struct {
@@ -247,6 +249,18 @@ ion_status ion_read_trace(ion_sim *sim, float *out, int64_t max_samples, int64_t
  * rows per CSR tile and the lanes-per-row scale.  *chosen (nullable) receives the table.
  * Not for ION_FLAG_PERSISTENT handles.  Synchronises. */
 ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
+
+/* Storage the handle streams per stored edge of a CSR network (host-copied CSR only; a
+ * borrowed device CSR is used as given):
+ *   *index_bytes  2 when every column is kept as its low 16 bits (the network has at most
+ *                 65 536 cells, or V_dend is staged in shared memory in chunks of 32 768
+ *                 cells, so the column relative to its chunk fits in 16 bits), else 4;
+ *   *weight_bytes 0 when every weight is bitwise equal (one scalar is kept), else 4;
+ *   *staged       1 when V_dend is staged in shared memory chunk by chunk, else 0.
+ * Both compactions are exact: the kernels evaluate the same edges with the same values.
+ * ION_FLAG_CSR_AS_GIVEN turns them off.  Dense / NGJ handles report 0, 0, 0.  Any output
+ * pointer may be NULL. */
+ion_status ion_csr_layout(const ion_sim *sim, int32_t *index_bytes, int32_t *weight_bytes, int32_t *staged);
 
 /* Steps taken so far (the absolute index of the next step). */
 int64_t ion_step_count(const ion_sim *sim);

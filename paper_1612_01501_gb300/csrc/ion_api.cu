@@ -105,6 +105,16 @@ extern "C" const char *ion_last_error(const ion_sim *s) {
     return s ? s->err.c_str() : g_last_error.c_str();
 }
 
+extern "C" ion_status ion_csr_layout(const ion_sim *s, int32_t *index_bytes, int32_t *weight_bytes, int32_t *staged) {
+    if (!s) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_csr_layout: NULL handle");
+    const bool csr = s->kind == ION_CSR && !s->d_map;
+    const bool c16 = csr && s->d_col16 != nullptr && (s->csr_staged || s->n <= 65536);
+    if (index_bytes) *index_bytes = csr ? (c16 ? 2 : 4) : 0;
+    if (weight_bytes) *weight_bytes = csr && s->d_w ? 4 : 0;
+    if (staged) *staged = csr ? s->csr_staged : 0;
+    return ION_OK;
+}
+
 extern "C" int64_t ion_step_count(const ion_sim *s) { return s ? s->t : -1; }
 extern "C" int64_t ion_launch_count(const ion_sim *s) { return s ? s->launches : -1; }
 
@@ -242,9 +252,19 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
 // 1024).  Only
 // CSR arrays copied from the host are staged: their columns were checked to be sorted
 // and in range, which the chunk boundaries rely on.
+// Connectivity fields of a CSR launch.  The 16-bit columns serve the staged kernel (columns
+// relative to a chunk of at most 2^16 cells) and the direct kernel when n <= 65 536.
+void ion_csr_fill(const ion_sim *s, CsrArgs &a, bool staged) {
+    a.row_ptr = s->d_rowptr;
+    a.col = s->d_col;
+    a.w = s->d_w;
+    a.g = s->g;
+    a.col16 = (s->d_col16 != nullptr && (staged || s->n <= 65536)) ? s->d_col16 : nullptr;
+}
+
 ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     const double deg = s->n > 0 ? (double)s->nnz / s->n : 0.0;
-    const double csr_bytes = 8.0 * (double)s->nnz;
+    const double csr_bytes = (double)((s->d_col16 ? 2 : 4) + (s->d_w ? 4 : 0)) * (double)s->nnz;
     const bool on = mode == 2 || (mode == 0 && deg >= 64.0 && csr_bytes > 96.0e6);
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
@@ -265,8 +285,7 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     CsrArgs probe{};
     probe.c.n = s->n;
     probe.c.n_pad = s->n_pad;
-    probe.col = s->d_col;
-    probe.w = s->d_w;
+    ion_csr_fill(s, probe, true);
     cudaError_t e = launch_csr_chunk_step(probe, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, true, s->st);
     if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
     s->csr_staged = 1;
@@ -287,6 +306,8 @@ void ion_sim_free_device(ion_sim *s) {
         cudaFree(s->d_col);
         cudaFree(s->d_w);
     }
+    cudaFree(s->d_col16);
+    s->d_col16 = nullptr;
     cudaFree(s->d_poff);
     cudaFree(s->d_pbeg);
     cudaFree(s->d_pend);
@@ -409,15 +430,34 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
             s->d_w = const_cast<float *>(conn->weight);
         } else {
             s->own_csr = true;
+            const bool compact = !(s->flags & ION_FLAG_CSR_AS_GIVEN);
+            // every weight bitwise equal: keep one scalar (the kernels multiply the row sum by it)
+            bool keep_w = conn->weight != nullptr && s->nnz > 0;
+            if (keep_w && compact) {
+                uint32_t b0, be;
+                std::memcpy(&b0, conn->weight, sizeof b0);
+                bool all = true;
+                for (int64_t q = 1; q < s->nnz && all; ++q) {
+                    std::memcpy(&be, conn->weight + q, sizeof be);
+                    all = be == b0;
+                }
+                if (all) {
+                    s->g = conn->weight[0];
+                    keep_w = false;
+                }
+            }
             e = cudaMalloc(&s->d_rowptr, (size_t)(s->n + 1) * sizeof(int32_t));
             if (e == cudaSuccess && s->nnz > 0) e = cudaMalloc(&s->d_col, (size_t)s->nnz * sizeof(int32_t));
-            if (e == cudaSuccess && s->nnz > 0 && conn->weight) e = cudaMalloc(&s->d_w, (size_t)s->nnz * sizeof(float));
+            if (e == cudaSuccess && keep_w) e = cudaMalloc(&s->d_w, (size_t)s->nnz * sizeof(float));
+            // the low 16 bits of every column, padded to whole 16-byte groups
+            if (e == cudaSuccess && s->nnz > 0 && compact) e = cudaMalloc(&s->d_col16, (size_t)round_up(s->nnz, 8) * sizeof(uint16_t));
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: CSR allocation: %s", cudaGetErrorString(e)));
             e = cudaMemcpyAsync(s->d_rowptr, conn->row_ptr, (size_t)(s->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
             if (e == cudaSuccess && s->nnz > 0)
                 e = cudaMemcpyAsync(s->d_col, conn->col_idx, (size_t)s->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
             if (e == cudaSuccess && s->d_w)
                 e = cudaMemcpyAsync(s->d_w, conn->weight, (size_t)s->nnz * sizeof(float), cudaMemcpyHostToDevice, s->st);
+            if (e == cudaSuccess && s->d_col16) e = launch_csr_col16(s->d_col, s->nnz, round_up(s->nnz, 8), s->d_col16, s->st);
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: CSR copy: %s", cudaGetErrorString(e)));
         }
         int SW, rows;
@@ -576,10 +616,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
     } else if (s->kind == ION_CSR) {
         CsrArgs a{};
         a.c = c;
-        a.row_ptr = s->d_rowptr;
-        a.col = s->d_col;
-        a.w = s->d_w;
-        a.g = s->g;
+        ion_csr_fill(s, a, s->csr_staged && !split);
         a.fuse = split ? 0 : 1;
         a.ic_out = s->d_ic;
         a.vd_in = nullptr;

@@ -64,6 +64,10 @@ __device__ __forceinline__ uint32_t ld_acquire_gpu(const uint32_t *p) {
     return v;
 }
 
+__device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Every CTA arrives once per barrier on a monotonically increasing counter (zeroed before
 // the launch); barrier k completes when the counter reaches k * gridDim.x.  A wait that
 // exceeds timeout_ns (or 2^30 polls) sets `status` bit 2 (timeout) and the shared abort
@@ -74,20 +78,25 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *abort_fl
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        atomicAdd(count, 1u);
-        const uint64_t t0 = globaltimer_ns();
-        for (uint32_t it = 0;; ++it) {
-            if (ld_acquire_gpu(count) >= target) break;
-            if (ld_acquire_gpu(abort_flag) != 0u) {
-                ok = 0;
-                break;
-            }
-            if ((it & 63u) == 63u && (globaltimer_ns() - t0 > timeout_ns || it > (1u << 30))) {
-                atomicOr(status, 2u);
-                atomicExch(abort_flag, 1u);
-                ok = 0;
-                break;
+        // release at GPU scope: the CTA's writes, ordered before this by the bar.sync above,
+        // become visible before the arrival does
+        red_release_gpu_add(count, 1u);
+        if (ld_acquire_gpu(count) < target) {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 1;; ++it) {
+                if (ld_acquire_gpu(count) >= target) break;
+                if ((it & 63u) == 0u) {          // the abort word and the clock every 64 polls
+                    if (ld_acquire_gpu(abort_flag) != 0u) {
+                        ok = 0;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > timeout_ns || it > (1u << 30)) {
+                        atomicOr(status, 2u);
+                        atomicExch(abort_flag, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
             }
         }
         // order the async-proxy (bulk copy) reads that follow after the acquire above

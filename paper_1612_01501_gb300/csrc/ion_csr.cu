@@ -20,7 +20,7 @@ namespace ion {
 
 // One CTA of 256 threads owns `rows` consecutive rows (rows <= 256).  Phase 1: groups of
 // SW lanes take the rows round-robin; phase 2: thread t updates row t.
-template <int SW, bool VEC, bool HAS_W>
+template <int SW, bool VEC, bool HAS_W, bool C16>
 __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows) {
     __shared__ float ic_s[256];
     const StepCommon &c = a.c;
@@ -31,12 +31,22 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     float *vnext = a.fuse ? vd_next(c, t) : nullptr;
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (rows + nsub - 1) / nsub;          // the same for every lane (shuffles below)
+    // the cell state of this thread's phase-2 row, loaded now so its latency overlaps phase 1
+    const int i_upd = row0 + (int)threadIdx.x;
+    const bool upd = a.fuse && (int)threadIdx.x < rows && i_upd < n;
+    Cell cell{};
+    if (upd) cell = load_cell(c.S, vcur, i_upd);
     for (int it = 0; it < iters; ++it) {
         const int rr = sub + it * nsub;
         const int i = row0 + rr;
         float acc = 0.0f;
-        if (rr < rows && i < n)
-            acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li);
+        if (rr < rows && i < n) {
+            if (C16)
+                acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li,
+                                                      VjGlobal{vcur});
+            else
+                acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li);
+        }
 #pragma unroll
         for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (li == 0 && rr < rows) ic_s[rr] = (HAS_W ? acc : acc * a.g) * (1.0f / GJ_SCALE);
@@ -46,25 +56,26 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     const int i = row0 + threadIdx.x;
     if (i >= n) return;
     const float ic = ic_s[threadIdx.x];
-    if (!a.fuse) {
+    if (!upd) {
         a.ic_out[i] = ic;
         return;
     }
-    const Cell cell = load_cell(c.S, vcur, i);
     float iapp = pulse_current(c.pulses, i, t);
     if (c.iapp != nullptr) iapp += c.iapp[i];
     const CellNext o = cell_step(c.P, cell, ic, iapp);
     finish_cell(c, t, vnext, i, o);
 }
 
-template <int SW, bool VEC, bool HAS_W>
+template <int SW, bool VEC, bool HAS_W, bool C16 = false>
 static cudaError_t launch_csr_T(const CsrArgs &a, int rows, cudaStream_t st) {
     const int grid = (a.c.n + rows - 1) / rows;
-    csr_step_kernel<SW, VEC, HAS_W><<<grid, 256, 0, st>>>(a, rows);
+    csr_step_kernel<SW, VEC, HAS_W, C16><<<grid, 256, 0, st>>>(a, rows);
     return cudaGetLastError();
 }
 template <int SW>
 static cudaError_t launch_csr_SW(const CsrArgs &a, int rows, cudaStream_t st) {
+    if (a.col16 != nullptr)   // 16-byte aligned indices (and weights, checked at creation)
+        return a.w != nullptr ? launch_csr_T<SW, true, true, true>(a, rows, st) : launch_csr_T<SW, true, false, true>(a, rows, st);
     const bool vec = ((uintptr_t)a.col % 16 == 0) && (a.w == nullptr || (uintptr_t)a.w % 16 == 0);
     if (a.w != nullptr) return vec ? launch_csr_T<SW, true, true>(a, rows, st) : launch_csr_T<SW, false, true>(a, rows, st);
     return vec ? launch_csr_T<SW, true, false>(a, rows, st) : launch_csr_T<SW, false, false>(a, rows, st);
@@ -87,10 +98,12 @@ cudaError_t launch_csr_step(const CsrArgs &a, int SW, int rows, cudaStream_t st)
 // Prefer L1 over shared memory for the V_dend gathers (the kernel uses 1 KB of shared).
 template <int SW>
 static void carveout_SW() {
-    cudaFuncSetAttribute(csr_step_kernel<SW, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaFuncSetAttribute(csr_step_kernel<SW, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaFuncSetAttribute(csr_step_kernel<SW, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-    cudaFuncSetAttribute(csr_step_kernel<SW, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, false, true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, false, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 cudaError_t prepare_csr_step() {
     carveout_SW<1>();
@@ -110,7 +123,7 @@ cudaError_t prepare_csr_step() {
 // rows whose columns fall in that chunk (the per-row chunk boundaries are precomputed:
 // mid[(c-1) * n + i] is the first edge of row i in chunk c).  The gathers then hit shared
 // memory while the indices and weights stream from HBM.
-template <int SW, bool VEC, bool HAS_W>
+template <int SW, bool VEC, bool HAS_W, bool C16>
 __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, int rows, const int32_t *mid,
                                                               int n_chunks) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -154,7 +167,11 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             if (rr < rows && i < n) {
                 const int e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
                 const int e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
-                acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vcur[i], li);
+                if (C16)
+                    acc = csr_row_sum16<SW, HAS_W, true>(a.col16, a.w, e0, e1, vcur[i], li,
+                                                         VjChunk{vs, (uint32_t)c0 & 0xFFFFu});
+                else
+                    acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vcur[i], li);
             }
 #pragma unroll
             for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -180,15 +197,15 @@ size_t csr_chunk_smem_bytes(int n_pad, int rows) {
     return (size_t)(n_pad < CSR_CHUNK ? n_pad : CSR_CHUNK) * sizeof(float) + (size_t)rows * sizeof(float);
 }
 
-template <int SW, bool VEC, bool HAS_W>
+template <int SW, bool VEC, bool HAS_W, bool C16 = false>
 static cudaError_t chunk_T(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
                            cudaStream_t st) {
     const size_t smem = csr_chunk_smem_bytes(a.c.n_pad, rows);
     if (prepare)
-        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem);
+        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (a.c.n + rows - 1) / rows;
-    csr_chunk_step_kernel<SW, VEC, HAS_W><<<grid, 1024, smem, st>>>(a, rows, mid, n_chunks);
+    csr_chunk_step_kernel<SW, VEC, HAS_W, C16><<<grid, 1024, smem, st>>>(a, rows, mid, n_chunks);
     return cudaGetLastError();
 }
 template <int SW>
@@ -200,8 +217,13 @@ static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int 
         if (e == cudaSuccess) e = chunk_T<SW, false, true>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, true, false>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, false, false>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, true, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, false, true>(a, rows, mid, n_chunks, true, st);
         return e;
     }
+    if (a.col16 != nullptr)
+        return a.w != nullptr ? chunk_T<SW, true, true, true>(a, rows, mid, n_chunks, false, st)
+                              : chunk_T<SW, true, false, true>(a, rows, mid, n_chunks, false, st);
     if (a.w != nullptr)
         return vec ? chunk_T<SW, true, true>(a, rows, mid, n_chunks, false, st)
                    : chunk_T<SW, false, true>(a, rows, mid, n_chunks, false, st);
@@ -245,6 +267,17 @@ cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, 
                                     cudaStream_t st) {
     if (n_chunks <= 1) return cudaSuccess;
     csr_chunk_bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, col, n, n_chunks, mid);
+    return cudaGetLastError();
+}
+
+// ---- compact column layout: the low 16 bits of every column (zero padding to 8 entries)
+__global__ void csr_col16_kernel(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n_alloc) col16[e] = e < nnz ? (uint16_t)((uint32_t)col[e] & 0xFFFFu) : (uint16_t)0;
+}
+cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st) {
+    if (n_alloc <= 0) return cudaSuccess;
+    csr_col16_kernel<<<(unsigned)((n_alloc + 255) / 256), 256, 0, st>>>(col, nnz, n_alloc, col16);
     return cudaGetLastError();
 }
 

@@ -70,4 +70,47 @@ __device__ __forceinline__ float csr_row_sum_smem(const float *vs, int c0, const
     return acc;
 }
 
+// 16-bit column indices: col16[e] holds the low 16 bits of column e (exact when the
+// network has at most 65 536 cells; chunk-relative below).  The body of a row is read
+// eight edges per lane with one 16-byte load of indices (and two of weights); vj maps a
+// 16-bit index to V_dend of that column.  LD_STREAM: the indices are read once per step
+// (evict-first), else through the read-only cache.
+template <int SW, bool HAS_W, bool LD_STREAM, class VJ>
+__device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col16, const float *__restrict__ w,
+                                               int e0, int e1, float vi, int li, VJ vj) {
+    float acc = 0.0f;
+    const int ea = min(e1, (e0 + 7) & ~7);                 // first 16-byte aligned edge
+    const int eb = ea + ((e1 - ea) & ~7);                   // end of the aligned body
+    for (int e = e0 + li; e < ea; e += SW) acc += gj_edge(vi, vj(col16[e]), HAS_W ? __ldg(w + e) : 1.0f);
+    for (int e = ea + 8 * li; e < eb; e += 8 * SW) {
+        const uint4 q = LD_STREAM ? __ldcs(reinterpret_cast<const uint4 *>(col16 + e))
+                                  : __ldg(reinterpret_cast<const uint4 *>(col16 + e));
+        float4 wa = make_float4(1.0f, 1.0f, 1.0f, 1.0f), wb = wa;
+        if (HAS_W) {
+            wa = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e)) : __ldg(reinterpret_cast<const float4 *>(w + e));
+            wb = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e + 4))
+                           : __ldg(reinterpret_cast<const float4 *>(w + e + 4));
+        }
+        const float v0 = vj(q.x & 0xFFFFu), v1 = vj(q.x >> 16), v2 = vj(q.y & 0xFFFFu), v3 = vj(q.y >> 16);
+        const float v4 = vj(q.z & 0xFFFFu), v5 = vj(q.z >> 16), v6 = vj(q.w & 0xFFFFu), v7 = vj(q.w >> 16);
+        acc += ((gj_edge(vi, v0, wa.x) + gj_edge(vi, v1, wa.y)) + (gj_edge(vi, v2, wa.z) + gj_edge(vi, v3, wa.w))) +
+               ((gj_edge(vi, v4, wb.x) + gj_edge(vi, v5, wb.y)) + (gj_edge(vi, v6, wb.z) + gj_edge(vi, v7, wb.w)));
+    }
+    for (int e = eb + li; e < e1; e += SW) acc += gj_edge(vi, vj(col16[e]), HAS_W ? __ldg(w + e) : 1.0f);
+    return acc;
+}
+
+// V_dend of a full 16-bit column index, from global memory (networks of <= 65 536 cells)
+struct VjGlobal {
+    const float *v;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return __ldg(v + j); }
+};
+// V_dend of a column of the shared-memory chunk starting at c0 (a multiple of 32 768):
+// the column is c0 + ((j - c0) mod 2^16) and lies in the chunk, so the low 16 bits suffice
+struct VjChunk {
+    const float *vs;
+    uint32_t c0lo;   // c0 mod 2^16
+    __device__ __forceinline__ float operator()(uint32_t j) const { return vs[(j - c0lo) & 0xFFFFu]; }
+};
+
 }  // namespace ion

@@ -22,7 +22,8 @@
 namespace ion {
 
 constexpr float HALF_PAD_U = 1.0e6f;   // 2^{-PAD^2} is exactly 0
-constexpr int HALF_CHUNK = 1024;       // tile columns per column-partial round
+constexpr int HALF_LOADS = 8;          // independent loads in flight per thread when gathering or reducing
+constexpr int HALF_SMEM_BUDGET = 220 * 1024;   // dynamic shared memory per CTA (one CTA per SM)
 
 __device__ __forceinline__ int half_partners(int c, int G) {   // D_c: blocks after c taken as columns
     const int D = (G - 1) / 2;
@@ -36,7 +37,7 @@ template <int R, int GJ>
 __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
     extern __shared__ __align__(16) float hsm[];
     __shared__ float red_s[32], red_c[32];
-    __shared__ float m_sh, U_sh;
+    __shared__ float U_sh;
     __shared__ int ok_sh;
 
     const StepCommon &c = a.c;
@@ -49,9 +50,10 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
     const int Dc = half_partners(cta, G);
     const int L = (Dc + 1) * b;                            // own block + D_c partner blocks
     const int Lp = (L + 127) / 128 * 128;                   // whole float4 rounds of 32 lanes
+    const int CH = a.chunk;                                 // tile columns per column-partial round
     float *tile = hsm;                                      // [a.colsum_stride]  -u_j of the column tile
-    float *colpart = tile + a.colsum_stride;                // [GR][HALF_CHUNK]
-    float *part = colpart + GR * HALF_CHUNK;                // [b] row sums of own rows
+    float *colpart = tile + a.colsum_stride;                // [GR][CH]
+    float *part = colpart + GR * CH;                        // [b] row sums of own rows
     float *colsum_me = a.colsum + (int64_t)cta * a.colsum_stride;
 
     const int row0 = cta * b;
@@ -78,22 +80,31 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
     for (int k = 0; k < a.n_steps && ok; ++k) {
         const int64_t t = t0 + k;
         const float *vcur = vd_slot(c.S, t);
-        if (threadIdx.x == 0) m_sh = __ldcg(vcur);
-        __syncthreads();
-        const float m = m_sh;
-        // stage the column tile: own block, then the partner blocks (wrapping), as -u
+        const float m = __ldcg(vcur);      // the shift, loaded by every thread with its tile loads
+        // stage the column tile: own block, then the partner blocks (wrapping), as -u;
+        // HALF_LOADS loads per thread are issued before any is used
         float Us = 0.0f, Uc = 0.0f;   // this thread's share of the own block's sum of u
-        for (int q = threadIdx.x; q < Lp; q += blockDim.x) {
-            float v = -HALF_PAD_U;
-            if (q < L) {
+        for (int q0 = 0; q0 < Lp; q0 += HALF_LOADS * (int)blockDim.x) {
+            float vv[HALF_LOADS];
+#pragma unroll
+            for (int j = 0; j < HALF_LOADS; ++j) {
+                const int q = q0 + j * (int)blockDim.x + (int)threadIdx.x;
                 const int row = (row0 + q) % P;
-                if (row < n) {
-                    const float u = (__ldcg(vcur + row) - m) * GJ_SCALE;
-                    v = -u;
-                    if (q < b) kahan_add(Us, Uc, u);
+                vv[j] = (q < L && row < n) ? __ldcg(vcur + row) : 0.0f;
+            }
+#pragma unroll
+            for (int j = 0; j < HALF_LOADS; ++j) {
+                const int q = q0 + j * (int)blockDim.x + (int)threadIdx.x;
+                if (q < Lp) {
+                    float v = -HALF_PAD_U;
+                    if (q < L && (row0 + q) % P < n) {
+                        const float u = (vv[j] - m) * GJ_SCALE;
+                        v = -u;
+                        if (q < b) kahan_add(Us, Uc, u);
+                    }
+                    tile[q] = v;
                 }
             }
-            tile[q] = v;
         }
         __syncthreads();
         float ui[R];
@@ -103,14 +114,14 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
 #pragma unroll
         for (int r = 0; r < R; ++r) ks[r] = kc[r] = 0.0f;
         const float4 *t4 = reinterpret_cast<const float4 *>(tile);
-        for (int ch = 0; ch * HALF_CHUNK < Lp; ++ch) {
-            const int nq = min(HALF_CHUNK, Lp - ch * HALF_CHUNK);   // columns in this chunk
+        for (int ch = 0; ch * CH < Lp; ++ch) {
+            const int nq = min(CH, Lp - ch * CH);                   // columns in this chunk
             const int G4 = nq / 4;                                  // float4 columns
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
             for (int m4 = cs * 32 + lane; m4 < G4; m4 += 32 * GJ) {
-                const float4 v = t4[ch * (HALF_CHUNK / 4) + m4];
+                const float4 v = t4[ch * (CH / 4) + m4];
                 const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
                 float2 ca = make_float2(0.0f, 0.0f), cb = make_float2(0.0f, 0.0f);
 #pragma unroll
@@ -127,16 +138,25 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
                     ca = __ffma2_rn(ea, da, ca);
                     cb = __ffma2_rn(eb, db, cb);
                 }
-                reinterpret_cast<float4 *>(colpart + rg * HALF_CHUNK)[m4] = make_float4(ca.x, ca.y, cb.x, cb.y);
+                reinterpret_cast<float4 *>(colpart + rg * CH)[m4] = make_float4(ca.x, ca.y, cb.x, cb.y);
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) kahan_add(ks[r], kc[r], acc[r].x + acc[r].y);
             __syncthreads();
-            // column sums of this chunk: the R-row groups summed in a fixed order
+            // column sums of this chunk: the R-row groups summed in ascending order (loads
+            // issued HALF_LOADS at a time)
             for (int q = threadIdx.x; q < nq; q += blockDim.x) {
                 float s = 0.0f;
-                for (int g = 0; g < GR; ++g) s += colpart[g * HALF_CHUNK + q];
-                colsum_me[ch * HALF_CHUNK + q] = s;
+                int g = 0;
+                for (; g + HALF_LOADS <= GR; g += HALF_LOADS) {
+                    float v[HALF_LOADS];
+#pragma unroll
+                    for (int j = 0; j < HALF_LOADS; ++j) v[j] = colpart[(g + j) * CH + q];
+#pragma unroll
+                    for (int j = 0; j < HALF_LOADS; ++j) s += v[j];
+                }
+                for (; g < GR; ++g) s += colpart[g * CH + q];
+                colsum_me[ch * CH + q] = s;
             }
             __syncthreads();
         }
@@ -175,19 +195,63 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
         bar_target += G;
         ok = grid_barrier(a.bar_count, a.abort_flag, bar_target, a.timeout_ns, c.status, &ok_sh);
         if (!ok) break;
-        if (threadIdx.x == 0) {
+        // sum of u over all cells: warp 0, lane-strided Kahan sums then a butterfly
+        if (warp == 0) {
             float s = 0.0f, cc = 0.0f;
-            for (int q = 0; q < G; ++q) kahan_add(s, cc, __ldcg(a.usum + q));
-            U_sh = s - cc;
-        }
-        __syncthreads();
-        if (row_thread) {
-            const int r = threadIdx.x;
-            float s = part[r], cc = 0.0f;
-            for (int d = 1; d <= G / 2; ++d) {            // CTA cta - d took this block at distance d
-                const int src = (cta - d + G) % G;
-                if (half_has(src, d, G)) kahan_add(s, cc, -__ldcg(a.colsum + (int64_t)src * a.colsum_stride + d * b + r));
+            for (int q0 = 0; q0 < G; q0 += 32 * HALF_LOADS) {
+                float vv[HALF_LOADS];
+#pragma unroll
+                for (int j = 0; j < HALF_LOADS; ++j) {
+                    const int q = q0 + 32 * j + lane;
+                    vv[j] = q < G ? __ldcg(a.usum + q) : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < HALF_LOADS; ++j) kahan_add(s, cc, vv[j]);
             }
+            float v = s - cc;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0) U_sh = v;
+        }
+        // the negated column sums other CTAs computed for this block: CTA cta - d took it at
+        // distance d; all threads load them (HALF_LOADS in flight each) into shared memory,
+        // then each row thread adds them in ascending d (0 where the source did not take it)
+        const int r = threadIdx.x;
+        float s = row_thread ? part[r] : 0.0f, cc = 0.0f;
+        const int slab = (GR * CH) / b;                 // distances per round (>= 128 / R)
+        for (int d0 = 1; d0 <= G / 2; d0 += slab) {
+            const int nd = min(slab, G / 2 - d0 + 1), tot = nd * b;
+            for (int i0 = 0; i0 < tot; i0 += HALF_LOADS * (int)blockDim.x) {
+                float vv[HALF_LOADS];
+#pragma unroll
+                for (int j = 0; j < HALF_LOADS; ++j) {
+                    const int idx = i0 + j * (int)blockDim.x + (int)threadIdx.x;
+                    const int d = d0 + idx / b, src = (cta - d + G) % G;
+                    vv[j] = (idx < tot && half_has(src, d, G))
+                                ? __ldcg(a.colsum + (int64_t)src * a.colsum_stride + d * b + idx % b)
+                                : 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < HALF_LOADS; ++j) {
+                    const int idx = i0 + j * (int)blockDim.x + (int)threadIdx.x;
+                    if (idx < tot) colpart[idx] = vv[j];
+                }
+            }
+            __syncthreads();
+            if (row_thread) {
+                int dd = 0;
+                for (; dd + HALF_LOADS <= nd; dd += HALF_LOADS) {
+                    float v[HALF_LOADS];
+#pragma unroll
+                    for (int j = 0; j < HALF_LOADS; ++j) v[j] = colpart[(dd + j) * b + r];
+#pragma unroll
+                    for (int j = 0; j < HALF_LOADS; ++j) kahan_add(s, cc, -v[j]);
+                }
+                for (; dd < nd; ++dd) kahan_add(s, cc, -colpart[dd * b + r]);
+            }
+            __syncthreads();
+        }
+        if (row_thread) {
             const float S = s - cc;
             const float u_i = (cell.vd - m) * GJ_SCALE;
             const float lin = fmaf((float)n, u_i, -U_sh);
@@ -223,14 +287,31 @@ int half_colsum_stride(int G, int b) {
     const int D = (G - 1) / 2 + ((G % 2 == 0) ? 1 : 0);
     return ((D + 1) * b + 127) / 128 * 128;
 }
-size_t half_smem_bytes(int G, int b, int GR) {
-    return (size_t)(half_colsum_stride(G, b) + GR * HALF_CHUNK + b) * sizeof(float);
+// columns per column-partial round: the fewest rounds whose partials fit the budget, split
+// evenly in multiples of 128
+int half_chunk(int G, int b, int GR) {
+    const int stride = half_colsum_stride(G, b);
+    const int room = HALF_SMEM_BUDGET / (int)sizeof(float) - stride - b;
+    const int max_ch = room / GR / 128 * 128;
+    if (max_ch < 128) return 0;
+    const int rounds = (stride + max_ch - 1) / max_ch;
+    const int ch = ((stride + rounds - 1) / rounds + 127) / 128 * 128;
+    return ch < max_ch ? ch : max_ch;
+}
+size_t half_smem_bytes(int G, int b, int GR, int CH) {
+    return (size_t)(half_colsum_stride(G, b) + GR * CH + b) * sizeof(float);
 }
 
 template <int R, int GJ>
-static cudaError_t half_RG(const HalfArgs &a, int W, int G, bool launch, int *ok_out, cudaStream_t st) {
+static cudaError_t half_RG(const HalfArgs &a0, int W, int G, bool launch, int *ok_out, cudaStream_t st) {
     const int GR = W / GJ;
-    const size_t smem = half_smem_bytes(G, a.rows, GR);
+    HalfArgs a = a0;
+    a.chunk = half_chunk(G, a.rows, GR);
+    if (a.chunk < 128) {
+        *ok_out = 0;
+        return launch ? cudaErrorInvalidValue : cudaSuccess;
+    }
+    const size_t smem = half_smem_bytes(G, a.rows, GR, a.chunk);
     if (!launch) {
         cudaError_t e = cudaFuncSetAttribute(dense_half_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
@@ -243,7 +324,7 @@ static cudaError_t half_RG(const HalfArgs &a, int W, int G, bool launch, int *ok
         *ok_out = (G <= per_sm * sms) ? 1 : 0;
         return cudaSuccess;
     }
-    void *args[] = {const_cast<HalfArgs *>(&a)};
+    void *args[] = {&a};
     return cudaLaunchCooperativeKernel((const void *)dense_half_kernel<R, GJ>, dim3(G), dim3(W * 32), args, smem, st);
 }
 

@@ -13,6 +13,7 @@ namespace ion {
 // value, so padded pairs contribute exactly 0 to the exponential sum.
 constexpr int TJ = 8192;
 constexpr int CSR_CHUNK = 32768;   // floats of V_dend per shared-memory chunk (128 KB)
+static_assert(CSR_CHUNK <= 65536, "16-bit chunk-relative columns need chunks of at most 2^16 cells");
 constexpr int PAD_J = 256;
 constexpr float PAD_VOLT = 1.0e7f;
 
@@ -71,6 +72,7 @@ struct CsrArgs {
     StepCommon c;
     const int32_t *row_ptr;
     const int32_t *col;
+    const uint16_t *col16;   // non-NULL: the low 16 bits of every column (see ion_csr.cu)
     const float *w;       // NULL: every weight is g
     float g;
     int32_t fuse;
@@ -99,6 +101,7 @@ struct HalfArgs {
     float *colsum;         // [grid][colsum_stride] column sums of each CTA's tile (L2-resident)
     int32_t colsum_stride;
     float *usum;           // [grid] sum of u over each CTA's own rows
+    int32_t chunk;         // tile columns per column-partial round (a multiple of 128; set by the launcher)
 };
 struct CellArgs {
     StepCommon c;
@@ -111,6 +114,7 @@ cudaError_t launch_csr_step(const CsrArgs &a, int lanes_per_row, int rows_per_ct
 cudaError_t prepare_csr_step();
 cudaError_t launch_csr_chunk_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *mid,
                                   int n_chunks, bool prepare, cudaStream_t st);
+cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st);
 cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
                                     int32_t *mid, cudaStream_t st);
 size_t csr_chunk_smem_bytes(int n_pad, int rows);

@@ -761,10 +761,7 @@ static cudaError_t surrogate_step(ion_sim *s, int k_off, const float *iapp) {
     } else if (s->kind == ION_CSR) {
         CsrArgs a{};
         a.c = c;
-        a.row_ptr = s->d_rowptr;
-        a.col = s->d_col;
-        a.w = s->d_w;
-        a.g = s->g;
+        ion_csr_fill(s, a, false);
         a.fuse = 0;
         a.ic_out = s->d_ic;
         e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);

@@ -20,6 +20,7 @@ struct ion_sim {
     int32_t *d_rowptr = nullptr, *d_col = nullptr;
     float *d_w = nullptr;
     bool own_csr = false;
+    uint16_t *d_col16 = nullptr;    // low 16 bits of every column (compact CSR layout)
     // state and bookkeeping
     float *d_state = nullptr;       // 20 * stride floats
     float *d_ic = nullptr;          // gap currents (split mode)
@@ -78,6 +79,7 @@ struct ion_sim {
 };
 
 // shared helpers (ion_api.cu)
+void ion_csr_fill(const ion_sim *s, ion::CsrArgs &a, bool staged);
 ion_status ion_fail(ion_sim *s, ion_status code, const char *fmt, ...);
 ion::ModelF ion_model_to_f32(const ion_model &m, double dt);
 ion::StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp);

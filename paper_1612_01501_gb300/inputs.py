@@ -78,6 +78,12 @@ def pulses(cells, t0_ms: float, t1_ms: float, amp: float):
             np.full(m, amp, np.float32))
 
 
+def pulse_windows(cells, windows, amp: float):
+    """One pulse per cell and window [(t0_ms, t1_ms), ...], concatenated window by window."""
+    P = [pulses(cells, a, b, amp) for a, b in windows]
+    return tuple(np.concatenate([p[q] for p in P]) for q in range(4))
+
+
 # ---- connectivity ----------------------------------------------------------------
 
 def random_symmetric_csr(n: int, k: int, seed: int):
@@ -117,10 +123,10 @@ def junction_weight(g_ref: float, neighbours: float) -> float:
 
 # ---- the five workloads ----------------------------------------------------------
 
-def config(name: str, k: int | None = None) -> dict:
+def config(name: str, k: int | None = None, n: int | None = None) -> dict:
     """Synthetic input bundle of one workload.
 
-    Keys: n, kind ('dense' | 'csr'), g (dense weight), row_ptr/col/w (CSR), jitter
+    Keys: n, kind ('dense' | 'csr' | 'ngj'), g (dense weight), row_ptr/col/w (CSR), jitter
     (added to V_dend), pulses (or None), n_steps.
     """
     if name == "c1":   # 64 cells all-to-all, g_c = 0.04, pulse 6 uA/cm^2 to cells 0-7 at 100-110 ms
@@ -139,6 +145,22 @@ def config(name: str, k: int | None = None) -> dict:
         sub = random_subset(n, 0.2, 2)
         return dict(name=f"{name}_k{k}", n=n, kind="csr", k=k, row_ptr=row_ptr, col=col, w=w,
                     jitter=vdend_jitter(n, 2), pulses=pulses(sub, 50.0, 60.0, 6.0), n_steps=4000)
+    if name == "k3":   # uncoupled cells (NGJ, Sec. 2.3.3): the cell update alone, default 2^22 cells
+        n = (1 << 22) if n is None else n
+        sub = random_subset(n, 0.2, 3)
+        return dict(name=f"{name}_n{n}", n=n, kind="ngj", jitter=vdend_jitter(n, 3),
+                    pulses=pulses(sub, 5.0, 15.0, 6.0), n_steps=400)
+    if name == "c1_spiking":   # c1 with every cell pulsed at 100-110, 400-410 and 700-710 ms
+        n = 64
+        cells = np.arange(n)
+        return dict(name=name, n=n, kind="dense", g=float(np.float32(0.04)), jitter=vdend_jitter(n, 0),
+                    pulses=pulse_windows(cells, [(100.0, 110.0), (400.0, 410.0), (700.0, 710.0)], 6.0),
+                    n_steps=20000)
+    if name == "c3_spiking":   # the c3 network with every cell pulsed at 50-60 and 500-510 ms
+        base = config("c3", k=k)
+        base.update(name=f"c3_spiking_k{base['k']}",
+                    pulses=pulse_windows(np.arange(base["n"]), [(50.0, 60.0), (500.0, 510.0)], 6.0))
+        return base
     if name == "validation":   # Sec. 3: identical cells, a pulse to all cells for 500 steps
         n = 64
         return dict(name=name, n=n, kind="dense", g=float(np.float32(0.04)), jitter=np.zeros(n),

@@ -27,6 +27,7 @@ STATUS_NAMES = ("OK", "INVALID_ARG", "BAD_CSR", "OOM", "CUDA", "NONFINITE", "TIM
 DENSE_UNIFORM, CSR, NO_GJ = 0, 1, 2
 HOST, DEVICE = 0, 1
 FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SPLIT, FLAG_NO_HALF = 1, 2, 4, 8, 16, 32, 64
+FLAG_CSR_AS_GIVEN = 128
 INPUT_NONE, INPUT_PULSES, INPUT_DENSE = 0, 1, 2
 MLP_IN, MLP_HID, MLP_OUT = 2, 64, 24
 
@@ -106,6 +107,8 @@ _SIGS = {
     "ion_set_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "ion_read_trace": (ctypes.c_int, [ctypes.c_void_p, c_f32p, ctypes.c_int64, c_i64p]),
     "ion_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ion_csr_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
     "ion_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ion_tune)]),
     "ion_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "ion_set_step_count": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
@@ -355,6 +358,13 @@ def ion_autotune(h, steps: int = 20) -> dict:
     t = ion_tune()
     _check(lib().ion_autotune(h, int(steps), ctypes.byref(t)), h)
     return {k: int(getattr(t, k)) for k, _ in ion_tune._fields_}
+
+
+def ion_csr_layout(h) -> dict:
+    """Bytes per stored edge the handle streams (index, weight) and whether V_dend is staged."""
+    ib, wb, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ion_csr_layout(h, ctypes.byref(ib), ctypes.byref(wb), ctypes.byref(st)), h)
+    return {"index_bytes": ib.value, "weight_bytes": wb.value, "staged": st.value}
 
 
 def ion_step_count(h) -> int:
