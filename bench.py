@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--sim-steps", type=int, default=0, help="time steps per bench step (0: the workload's)")
-    ap.add_argument("--variant", default="auto", choices=["auto", "graph", "persistent", "persistent_full"])
+    ap.add_argument("--variant", default="auto",
+                    choices=["auto", "graph", "persistent", "persistent_half", "graph_csr_as_given"])
     ap.add_argument("--no-extra", action="store_true", help="skip the CPU baseline and the e2e leg")
     return ap.parse_args()
 
@@ -335,9 +336,9 @@ def main():
     surrogate_info = {}
     if key == "c5":
         t0 = time.perf_counter()
-        surrogate, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=30, batch=2048, lr=2e-3, seed=7,
+        surrogate, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=100, batch=2048, lr=2e-3, seed=7,
                                                   v_lo=-100.0, v_hi=50.0, ca_lo=1.36, ca_hi=13.5, stream=stream)
-        surrogate_info = {"train_seconds": time.perf_counter() - t0, "train_samples": 1 << 20, "epochs": 30,
+        surrogate_info = {"train_seconds": time.perf_counter() - t0, "train_samples": 1 << 20, "epochs": 100,
                           "final_loss_normalised": loss}
 
     def make_sim(flags):
@@ -398,8 +399,10 @@ def main():
     cand = [("graph", ion.FLAG_KAHAN)]
     if dense:
         cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
-        if n > 144:   # multi-CTA networks: the full pass as well as the half-work pass
-            cand.append(("persistent_full", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_NO_HALF))
+        if n > 144:   # multi-CTA networks: the half-work pass as well as the full pass
+            cand.append(("persistent_half", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK))
+    if cfg["kind"] == "csr" and key != "c5":   # the CSR as given (32-bit columns, per-edge weights) too
+        cand.append(("graph_csr_as_given", ion.FLAG_KAHAN | ion.FLAG_CSR_AS_GIVEN))
     if args.variant != "auto":
         cand = [c for c in cand if c[0] == args.variant]
     if key == "c5":
@@ -451,13 +454,13 @@ def main():
     elif dense:
         # SFU-bound: one ex2 per pair evaluation (N^2 per time step); the half-work kernel
         # evaluates each unordered pair once (N^2 / 2 ex2 per time step)
-        half = best == "persistent" and n > 144
+        half = best == "persistent_half"
         ex2_step = n * n / 2 if half else n * n
         peak = ion.ion_probe_peak(0, 4096, stream)
         achieved = ex2_step / per_step_s
         roof = {"bound": "alu", "unit": "ex2/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None, "kernel": {"persistent": "dense_half_kernel" if n > 144 else "dense_persist_kernel",
-                           "persistent_full": "dense_persist_kernel"}.get(best, "dense_step_kernel"),
+                "traffic": None, "kernel": {"persistent": "dense_persist_kernel",
+                           "persistent_half": "dense_half_kernel"}.get(best, "dense_step_kernel"),
                 "peak_source": "measured SFU ex2 rate (ion_probe_peak) in the same process",
                 "ffma_peak_per_s": ion.ion_probe_peak(1, 4096, stream), "us_per_timestep": per_step_s * 1e6,
                 "ex2_per_timestep": ex2_step}
@@ -493,13 +496,20 @@ def main():
         # state (15 words read + 18 written) and the pulse table (8 B per cell on average)
         nnz = len(cfg["col"])
         lay = ion.ion_csr_layout(sim.h)
-        n_chunks = (n + 32767) // 32768 if lay["staged"] else 1
-        bytes_step = ((lay["index_bytes"] + lay["weight_bytes"]) * nnz + 4 * (n + 1) + 4 * n * (n_chunks - 1)
-                      + 132 * n + 8 * n)
+        n_pad = (n + 255) // 256 * 256
+        if lay["staged"] == 2:    # chunk-major: row bounds of every chunk (n + 1 each)
+            ptr_bytes = 4 * (n + 1) * ((n_pad + 16383) // 16384)
+        elif lay["staged"] == 1:  # row-major: row pointers + interior chunk boundaries
+            ptr_bytes = 4 * (n + 1) + 4 * n * ((n_pad + 32767) // 32768 - 1)
+        else:
+            ptr_bytes = 4 * (n + 1)
+        bytes_step = (lay["index_bytes"] + lay["weight_bytes"]) * nnz + ptr_bytes + 132 * n + 8 * n
         achieved = bytes_step / per_step_s / 1e9
         peak = hbm_peak()
         roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None, "kernel": "csr_step_kernel", "algorithmic_bytes_per_timestep": bytes_step,
+                "traffic": None,
+                "kernel": ["csr_step_kernel", "csr_chunk_step_kernel", "csr_stream_kernel"][lay["staged"]],
+                "algorithmic_bytes_per_timestep": bytes_step,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6,
                 "note": "working set fits in L2 (129 MB)" if bytes_step < 100e6 else "streams from HBM",
                 "csr_layout": lay}

@@ -88,16 +88,15 @@ enum ion_mem { ION_HOST = 0, ION_DEVICE = 1 };
 enum ion_flag {
     ION_FLAG_KAHAN = 1u << 0,      /* compensated dense gap-junction sums (default on)     */
     ION_FLAG_PERSISTENT = 1u << 1, /* dense: one cooperative launch per ion_step call, state in
-                                      registers, bounded grid barriers per step (if every CTA
-                                      fits on the GPU at once; else per-step launches).  With
-                                      several CTAs each unordered pair is evaluated once
-                                      (I_ij = -I_ji) unless ION_FLAG_NO_HALF is set           */
+                                      registers, a bounded grid barrier per step (if every CTA
+                                      fits on the GPU at once; else per-step launches)       */
     ION_FLAG_SURROGATE = 1u << 2,  /* MLP surrogate for the channel rate functions         */
     ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
     ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
     ION_FLAG_SPLIT = 1u << 5,      /* separate gap-junction and cell-update kernels         */
-    ION_FLAG_NO_HALF = 1u << 6,    /* persistent dense: evaluate every ordered pair instead of
-                                      each unordered pair once (the default for >= 2 CTAs)  */
+    ION_FLAG_HALF_WORK = 1u << 6,  /* persistent dense with several CTAs: evaluate each unordered
+                                      pair once (I_ij = -I_ji), exchanging column sums through
+                                      L2 (two bounded barriers per step)                     */
     ION_FLAG_CSR_AS_GIVEN = 1u << 7 /* CSR: keep 32-bit columns and per-edge weights even when
                                       a compact layout applies (see ion_csr_layout)         */
 };
@@ -252,11 +251,14 @@ ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
 
 /* Storage the handle streams per stored edge of a CSR network (host-copied CSR only; a
  * borrowed device CSR is used as given):
- *   *index_bytes  2 when every column is kept as its low 16 bits (the network has at most
- *                 65 536 cells, or V_dend is staged in shared memory in chunks of 32 768
- *                 cells, so the column relative to its chunk fits in 16 bits), else 4;
+ *   *index_bytes  2 when every column is kept as its low 16 bits and used: V_dend is
+ *                 staged in shared memory in chunks of 32 768 cells (the column relative to
+ *                 its chunk fits in 16 bits), or the network has at most 65 536 cells and a
+ *                 mean degree of at least 32; else 4;
  *   *weight_bytes 0 when every weight is bitwise equal (one scalar is kept), else 4;
- *   *staged       1 when V_dend is staged in shared memory chunk by chunk, else 0.
+ *   *staged       1 when V_dend is staged in shared memory chunk by chunk (row-major CSR),
+ *                 2 when, in addition, the CSR is kept chunk-major and streamed by bulk
+ *                 copies (16-bit columns, compact layout), else 0.
  * Both compactions are exact: the kernels evaluate the same edges with the same values.
  * ION_FLAG_CSR_AS_GIVEN turns them off.  Dense / NGJ handles report 0, 0, 0.  Any output
  * pointer may be NULL. */

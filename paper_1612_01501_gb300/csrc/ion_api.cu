@@ -105,10 +105,12 @@ extern "C" const char *ion_last_error(const ion_sim *s) {
     return s ? s->err.c_str() : g_last_error.c_str();
 }
 
+static bool csr_use16(const ion_sim *s, bool staged);
+
 extern "C" ion_status ion_csr_layout(const ion_sim *s, int32_t *index_bytes, int32_t *weight_bytes, int32_t *staged) {
     if (!s) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_csr_layout: NULL handle");
     const bool csr = s->kind == ION_CSR && !s->d_map;
-    const bool c16 = csr && s->d_col16 != nullptr && (s->csr_staged || s->n <= 65536);
+    const bool c16 = csr && csr_use16(s, s->csr_staged != 0);
     if (index_bytes) *index_bytes = csr ? (c16 ? 2 : 4) : 0;
     if (weight_bytes) *weight_bytes = csr && s->d_w ? 4 : 0;
     if (staged) *staged = csr ? s->csr_staged : 0;
@@ -252,14 +254,21 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
 // 1024).  Only
 // CSR arrays copied from the host are staged: their columns were checked to be sorted
 // and in range, which the chunk boundaries rely on.
-// Connectivity fields of a CSR launch.  The 16-bit columns serve the staged kernel (columns
-// relative to a chunk of at most 2^16 cells) and the direct kernel when n <= 65 536.
+// The 16-bit columns serve the staged kernel (columns relative to a chunk of at most 2^16
+// cells) and the direct kernel when n <= 65 536 and rows are long enough (mean degree >= 32)
+// for its eight-edge groups; shorter rows read 32-bit columns four at a time.
+static bool csr_use16(const ion_sim *s, bool staged) {
+    if (s->d_col16 == nullptr) return false;
+    return staged || (s->n <= 65536 && s->nnz >= 32 * (int64_t)s->n);
+}
+
+// Connectivity fields of a CSR launch.
 void ion_csr_fill(const ion_sim *s, CsrArgs &a, bool staged) {
     a.row_ptr = s->d_rowptr;
     a.col = s->d_col;
     a.w = s->d_w;
     a.g = s->g;
-    a.col16 = (s->d_col16 != nullptr && (staged || s->n <= 65536)) ? s->d_col16 : nullptr;
+    a.col16 = csr_use16(s, staged) ? s->d_col16 : nullptr;
 }
 
 ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
@@ -269,6 +278,15 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
     if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr) return ION_OK;
+    // compact layout: the chunk-major CSR streamed by bulk copies, where it applies
+    if (s->d_col16) {
+        const ion_status st = s->stream_ns > 0 ? ION_OK : ion_setup_csr_stream(s);
+        if (st != ION_OK) return st;
+        if (s->stream_ns > 0) {
+            s->csr_staged = 2;
+            return ION_OK;
+        }
+    }
     s->n_chunks = (s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK;
     int rows = (s->n + s->sms - 1) / s->sms;
     if (rows > 1024) rows = 1024;
@@ -308,6 +326,12 @@ void ion_sim_free_device(ion_sim *s) {
     }
     cudaFree(s->d_col16);
     s->d_col16 = nullptr;
+    cudaFree(s->d_crp);
+    cudaFree(s->d_ccol);
+    cudaFree(s->d_cw);
+    s->d_crp = nullptr;
+    s->d_ccol = nullptr;
+    s->d_cw = nullptr;
     cudaFree(s->d_poff);
     cudaFree(s->d_pbeg);
     cudaFree(s->d_pend);
@@ -616,11 +640,13 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
     } else if (s->kind == ION_CSR) {
         CsrArgs a{};
         a.c = c;
-        ion_csr_fill(s, a, s->csr_staged && !split);
+        ion_csr_fill(s, a, s->csr_staged == 1 && !split);
         a.fuse = split ? 0 : 1;
         a.ic_out = s->d_ic;
         a.vd_in = nullptr;
-        if (s->csr_staged && !split)
+        if (s->csr_staged == 2 && !split)
+            e = launch_csr_stream(s, c, s->st);
+        else if (s->csr_staged == 1 && !split)
             e = launch_csr_chunk_step(a, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, false, s->st);
         else
             e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);

@@ -15,6 +15,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <numeric>
 #include <vector>
 
@@ -27,6 +28,9 @@
 namespace ion {
 
 enum TileKind : int32_t { TILE_DENSE = 0, TILE_CSR = 1 };
+// CSR tile modes: every weight of the network equals T.g; 16-bit network-local columns
+// (col16); the network's V_dend staged in shared memory (with TILE_C16)
+enum TileMode : int32_t { TILE_UNIFORM_W = 1, TILE_C16 = 2, TILE_STAGE_V = 4 };
 
 struct BatchTile {
     int32_t kind;
@@ -36,7 +40,8 @@ struct BatchTile {
     int32_t row0;    // first row (global cell index) of the tile
     int32_t rows;    // rows of the tile
     int32_t sw;      // CSR: lanes per row
-    float g;         // dense: pair weight
+    float g;         // dense: pair weight; CSR with TILE_UNIFORM_W: every edge weight
+    int32_t mode;    // CSR: TileMode bits
 };
 
 struct BatchArgs {
@@ -44,9 +49,53 @@ struct BatchArgs {
     const BatchTile *tiles;
     const int32_t *row_ptr;   // padded-index CSR of every CSR network (other rows empty)
     const int32_t *col;
+    const uint16_t *col16;    // network-local columns (TILE_C16 networks)
     const float *w;
     int32_t kahan;
 };
+
+// V_dend of a network-local column from shared memory (the network's staged copy)
+struct VjShared {
+    const float *vs;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return vs[j]; }
+};
+
+// CSR rows of a TILE_C16 tile: 16-bit local columns, V_dend from `vj` (staged or global)
+template <int SW, bool HAS_W, class VJ>
+__device__ __forceinline__ void batch_csr_rows16(const BatchArgs &a, const BatchTile &T, const float *vcur, VJ vj,
+                                                 float *ic_s) {
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    const int iters = (T.rows + nsub - 1) / nsub;
+    for (int it = 0; it < iters; ++it) {
+        const int rr = sub + it * nsub;
+        float acc = 0.0f;
+        if (rr < T.rows) {
+            const int i = T.row0 + rr;
+            acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li, vj);
+        }
+#pragma unroll
+        for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (li == 0 && rr < T.rows) ic_s[rr] = (HAS_W ? acc : acc * T.g) * (1.0f / GJ_SCALE);
+    }
+}
+template <int SW, class VJ>
+__device__ __forceinline__ void batch_csr_rows16_w(const BatchArgs &a, const BatchTile &T, const float *vcur, VJ vj,
+                                                   float *ic_s) {
+    if (T.mode & TILE_UNIFORM_W) batch_csr_rows16<SW, false>(a, T, vcur, vj, ic_s);
+    else batch_csr_rows16<SW, true>(a, T, vcur, vj, ic_s);
+}
+template <class VJ>
+__device__ __forceinline__ void batch_csr_tile16(const BatchArgs &a, const BatchTile &T, const float *vcur, VJ vj,
+                                                 float *ic_s) {
+    switch (T.sw) {
+        case 1: batch_csr_rows16_w<1>(a, T, vcur, vj, ic_s); break;
+        case 2: batch_csr_rows16_w<2>(a, T, vcur, vj, ic_s); break;
+        case 4: batch_csr_rows16_w<4>(a, T, vcur, vj, ic_s); break;
+        case 8: batch_csr_rows16_w<8>(a, T, vcur, vj, ic_s); break;
+        case 16: batch_csr_rows16_w<16>(a, T, vcur, vj, ic_s); break;
+        default: batch_csr_rows16_w<32>(a, T, vcur, vj, ic_s); break;
+    }
+}
 
 template <int SW>
 __device__ __forceinline__ void batch_csr_rows(const BatchArgs &a, const BatchTile &T, const float *vcur, float *ic_s) {
@@ -116,6 +165,27 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
             const int rr = threadIdx.x;
             ic_s[rr] = row_current<1>(sm, rr, (net_v[local0 + rr] - m_shift) * GJ_SCALE, T.n, U, T.g);
         }
+    } else if (T.mode & TILE_STAGE_V) {
+        // the network's V_dend (n_pad <= TJ floats) in shared memory, 16-bit local columns
+        float *vs = reinterpret_cast<float *>(smem_raw);
+        if (threadIdx.x == 0) {
+            mbar_init(&bar[0], 1);
+            fence_mbar_init();
+            mbar_expect_tx(&bar[0], (uint32_t)T.n_pad * 4u);
+            bulk_g2s(vs, vcur + T.seg, (uint32_t)T.n_pad * 4u, &bar[0]);
+        }
+        __syncthreads();
+        const bool landed = mbar_wait_bounded(&bar[0], 0u);
+        if (__syncthreads_or(!landed)) {
+            if (threadIdx.x == 0) {
+                atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+                (void)mbar_wait_bounded(&bar[0], 0u);
+            }
+            return;
+        }
+        batch_csr_tile16(a, T, vcur, VjShared{vs}, ic_s);
+    } else if (T.mode & TILE_C16) {
+        batch_csr_tile16(a, T, vcur, VjGlobal{vcur + T.seg}, ic_s);
     } else {
         switch (T.sw) {
             case 1: batch_csr_rows<1>(a, T, vcur, ic_s); break;
@@ -165,9 +235,11 @@ using namespace ion;
 // ---- host side -------------------------------------------------------------------------
 struct BatchNet {
     int32_t kind, n, n_pad, seg;
-    float g;
+    float g;          // dense: pair weight; CSR with uniform weights: every edge weight
     int64_t e0, nnz;  // CSR edges in the global arrays
     int sw;
+    bool uniform = false;   // CSR: every weight bitwise equal (g)
+    bool c16 = false;       // CSR: 16-bit network-local columns in col16
 };
 
 struct BatchExt {
@@ -201,15 +273,17 @@ static ion_status batch_plan(ion_sim *s) {
     for (const BatchNet &b : X->nets) {
         if (b.kind == ION_DENSE_UNIFORM) {
             for (int r = 0; r < b.n; r += drows) {
-                BatchTile T{TILE_DENSE, b.seg, b.n, b.n_pad, b.seg + r, std::min(drows, b.n - r), 0, b.g};
+                BatchTile T{TILE_DENSE, b.seg, b.n, b.n_pad, b.seg + r, std::min(drows, b.n - r), 0, b.g, 0};
                 tiles.push_back(T);
                 cost.push_back((double)T.rows * b.n_pad);
             }
         } else {
             const double deg = b.n > 0 ? (double)b.nnz / b.n : 0.0;
+            int mode = (b.uniform ? TILE_UNIFORM_W : 0) | (b.c16 ? TILE_C16 : 0);
+            if (b.c16 && b.n_pad <= X->max_dense_pad) mode |= TILE_STAGE_V;   // fits the launch's shared memory
             for (int r = 0; r < b.n; r += X->csr_rows) {
                 BatchTile T{TILE_CSR, b.seg, b.n, b.n_pad, b.seg + r, std::min(X->csr_rows, b.n - r),
-                            csr_sw_for(deg, X->sw_scale), 0.0f};
+                            csr_sw_for(deg, X->sw_scale), b.uniform ? b.g : 0.0f, mode};
                 tiles.push_back(T);
                 cost.push_back(3.0 * T.rows * deg + 60.0 * T.rows);
             }
@@ -261,6 +335,7 @@ static cudaError_t batch_step(ion_sim *s, int k_off, const float *iapp) {
     a.tiles = X->d_tiles;
     a.row_ptr = s->d_rowptr;
     a.col = s->d_col;
+    a.col16 = s->d_col16;
     a.w = s->d_w;
     a.kahan = 1;
     s->launches++;
@@ -371,7 +446,23 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
         x.g = N.kind == ION_DENSE_UNIFORM ? conns[b].g_c : 0.0f;
         x.e0 = nnz_total;
         x.nnz = N.kind == ION_CSR ? conns[b].nnz : 0;
-        if (N.kind == ION_DENSE_UNIFORM) max_pad = std::max(max_pad, x.n_pad);
+        if (N.kind == ION_CSR && !(params->flags & ION_FLAG_CSR_AS_GIVEN)) {
+            // compact layout: 16-bit local columns; one scalar when every weight is bitwise equal
+            x.c16 = N.n_cells <= 65536;
+            const ion_conn &C = conns[b];
+            x.uniform = true;
+            x.g = C.g_c;
+            if (C.weight && x.nnz > 0) {
+                uint32_t b0, be;
+                std::memcpy(&b0, C.weight, sizeof b0);
+                for (int64_t q = 1; q < x.nnz && x.uniform; ++q) {
+                    std::memcpy(&be, C.weight + q, sizeof be);
+                    x.uniform = be == b0;
+                }
+                x.g = C.weight[0];
+            }
+        }
+        if (N.kind == ION_DENSE_UNIFORM || (x.c16 && x.n_pad <= TJ)) max_pad = std::max(max_pad, x.n_pad);
         seg += x.n_pad;
         n_user += x.n;
         nnz_total += x.nnz;
@@ -409,14 +500,18 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     // global CSR over the padded index space
     std::vector<int32_t> rp((size_t)seg + 1, 0), col((size_t)std::max<int64_t>(nnz_total, 1));
     std::vector<float> w((size_t)std::max<int64_t>(nnz_total, 1));
+    std::vector<uint16_t> col16((size_t)(nnz_total + 8), 0);   // padded to whole 16-byte groups
+    bool any16 = false;
     for (int b = 0; b < n_nets; ++b) {
         const BatchNet &x = bn[(size_t)b];
         if (x.kind != ION_CSR) continue;
         const ion_conn &C = conns[b];
+        any16 = any16 || x.c16;
         for (int i = 0; i < x.n; ++i) rp[(size_t)x.seg + i + 1] = C.row_ptr[i + 1] - C.row_ptr[i];
         for (int64_t e = 0; e < x.nnz; ++e) {
             col[(size_t)(x.e0 + e)] = x.seg + C.col_idx[e];
             w[(size_t)(x.e0 + e)] = C.weight ? C.weight[e] : C.g_c;
+            if (x.c16) col16[(size_t)(x.e0 + e)] = (uint16_t)C.col_idx[e];
         }
     }
     for (size_t i = 0; i < (size_t)seg; ++i) rp[i + 1] += rp[i];
@@ -425,6 +520,7 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     cudaError_t e = cudaMalloc(&s->d_rowptr, rp.size() * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_col, col.size() * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_w, w.size() * sizeof(float));
+    if (e == cudaSuccess && any16) e = cudaMalloc(&s->d_col16, col16.size() * sizeof(uint16_t));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_map, X->h_map.size() * sizeof(int32_t));
     if (e == cudaSuccess) e = cudaMalloc(&X->d_tmp, (size_t)NF * n_user * sizeof(float));
     if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create_batch: %s", cudaGetErrorString(e)));
@@ -433,6 +529,8 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     e = cudaMemcpy(s->d_rowptr, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && any16)
+        e = cudaMemcpy(s->d_col16, col16.data(), col16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(s->d_map, X->h_map.data(), X->h_map.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create_batch: %s", cudaGetErrorString(e)));
@@ -590,10 +688,20 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         int b_csw = s->csr_chunk_SW;
         const int sw0 = s->csr_SW;
         for (int staged = 0; staged <= 1 && st == ION_OK; ++staged) {
-            if (staged && ion_setup_csr_staging(s, 2) != ION_OK) break;
-            s->csr_staged = staged;
+            if (staged) {   // the staged layout the handle supports (streamed or row-major)
+                if (ion_setup_csr_staging(s, 2) != ION_OK || s->csr_staged == 0) break;
+            } else {
+                s->csr_staged = 0;
+            }
+            const int mode = s->csr_staged;
+            bool timed_stream = false;
             for (int sw : SWs) {
-                if (sw * 4 < sw0 || sw > sw0 * 4) continue;   // near the degree-based choice
+                if (mode == 2) {                               // streamed: one warp per row, one shape
+                    if (timed_stream) continue;
+                    timed_stream = true;
+                } else if (sw * 4 < sw0 || sw > sw0 * 4) {
+                    continue;                                  // near the degree-based choice
+                }
                 for (int r : rows) {
                     if (staged && r != rows[0]) continue;     // staged: rows per CTA fixed by the SM count
                     if (staged) s->csr_chunk_SW = sw;
@@ -607,7 +715,7 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
                     if (st != ION_OK) break;
                     if (ms < best) {
                         best = ms;
-                        bstaged = staged;
+                        bstaged = mode;
                         if (staged) b_csw = sw;
                         else {
                             bsw = sw;
@@ -621,8 +729,8 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         s->csr_rows = brows;
         s->csr_staged = bstaged;
         s->csr_chunk_SW = b_csw;
-        bt.csr_lanes_per_row = bstaged ? b_csw : bsw;
-        bt.csr_rows_per_cta = bstaged ? s->csr_chunk_rows : brows;
+        bt.csr_lanes_per_row = bstaged == 2 ? 32 : bstaged ? b_csw : bsw;
+        bt.csr_rows_per_cta = bstaged == 2 ? s->stream_rows : bstaged ? s->csr_chunk_rows : brows;
         bt.csr_staging = bstaged ? 2 : 1;
     }
     if (s->gexec) {

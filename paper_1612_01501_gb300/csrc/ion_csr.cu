@@ -31,11 +31,6 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     float *vnext = a.fuse ? vd_next(c, t) : nullptr;
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (rows + nsub - 1) / nsub;          // the same for every lane (shuffles below)
-    // the cell state of this thread's phase-2 row, loaded now so its latency overlaps phase 1
-    const int i_upd = row0 + (int)threadIdx.x;
-    const bool upd = a.fuse && (int)threadIdx.x < rows && i_upd < n;
-    Cell cell{};
-    if (upd) cell = load_cell(c.S, vcur, i_upd);
     for (int it = 0; it < iters; ++it) {
         const int rr = sub + it * nsub;
         const int i = row0 + rr;
@@ -56,10 +51,11 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     const int i = row0 + threadIdx.x;
     if (i >= n) return;
     const float ic = ic_s[threadIdx.x];
-    if (!upd) {
+    if (!a.fuse) {
         a.ic_out[i] = ic;
         return;
     }
+    const Cell cell = load_cell(c.S, vcur, i);
     float iapp = pulse_current(c.pulses, i, t);
     if (c.iapp != nullptr) iapp += c.iapp[i];
     const CellNext o = cell_step(c.P, cell, ic, iapp);

@@ -30,10 +30,10 @@
 namespace ion {
 
 // ---- one launch per step ----------------------------------------------------------------
-// Launch bounds: up to 1024 threads (64 registers) when R <= 2, else 768.
+// Launch bounds: up to 1024 threads (64 registers) when R <= 4, else 768.
 template <int R>
 struct DenseBounds {
-    static constexpr int threads = R <= 2 ? 1024 : 768;
+    static constexpr int threads = R <= 4 ? 1024 : 768;
 };
 
 template <int R, int GJ>
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
 // 896 threads (72 registers) when R <= 2, else 576.
 template <int R>
 struct PersistBounds {
-    static constexpr int threads = R <= 2 ? 896 : 576;
+    static constexpr int threads = R <= 4 ? 896 : 576;
 };
 
 template <int R, int GJ>
@@ -335,7 +335,7 @@ cudaError_t persist_dense(const PersistArgs &a, int R, int W, int GJ, int *grid_
     return dispatch<PersistOp>(R, GJ, L);
 }
 
-int dense_max_threads(int R) { return R <= 2 ? 1024 : 768; }
-int persist_max_threads(int R) { return R <= 2 ? 896 : 576; }
+int dense_max_threads(int R) { return R <= 4 ? 1024 : 768; }
+int persist_max_threads(int R) { return R <= 4 ? 896 : 576; }
 
 }  // namespace ion

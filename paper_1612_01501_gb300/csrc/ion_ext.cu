@@ -106,7 +106,7 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
             // several CTAs: the half-work kernel, if its shape and grid fit
             const int rows = (s->persist_W / s->persist_GJ) * s->persist_R;
             const int grid = (s->n + rows - 1) / rows;
-            if (grid >= 2 && s->persist_R <= 4 && s->persist_W <= 28 && !(s->flags & ION_FLAG_NO_HALF)) {
+            if (grid >= 2 && s->persist_R <= 4 && s->persist_W <= 28 && (s->flags & ION_FLAG_HALF_WORK)) {
                 HalfArgs probe{};
                 probe.rows = rows;
                 int fits = 0;

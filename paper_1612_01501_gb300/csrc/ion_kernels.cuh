@@ -14,6 +14,7 @@ namespace ion {
 constexpr int TJ = 8192;
 constexpr int CSR_CHUNK = 32768;   // floats of V_dend per shared-memory chunk (128 KB)
 static_assert(CSR_CHUNK <= 65536, "16-bit chunk-relative columns need chunks of at most 2^16 cells");
+constexpr int CSR_SCHUNK = 16384;  // cells per chunk of the streamed (chunk-major) CSR kernel (64 KB)
 constexpr int PAD_J = 256;
 constexpr float PAD_VOLT = 1.0e7f;
 

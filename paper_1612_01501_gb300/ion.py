@@ -26,7 +26,7 @@ OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT,
 STATUS_NAMES = ("OK", "INVALID_ARG", "BAD_CSR", "OOM", "CUDA", "NONFINITE", "TIMEOUT", "UNSUPPORTED")
 DENSE_UNIFORM, CSR, NO_GJ = 0, 1, 2
 HOST, DEVICE = 0, 1
-FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SPLIT, FLAG_NO_HALF = 1, 2, 4, 8, 16, 32, 64
+FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SPLIT, FLAG_HALF_WORK = 1, 2, 4, 8, 16, 32, 64
 FLAG_CSR_AS_GIVEN = 128
 INPUT_NONE, INPUT_PULSES, INPUT_DENSE = 0, 1, 2
 MLP_IN, MLP_HID, MLP_OUT = 2, 64, 24

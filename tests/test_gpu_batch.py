@@ -90,10 +90,20 @@ def test_batch_matches_each_network_alone(cuda, O):
         off += n
 
 
-def test_batch_one_step_error(cuda, O):
+@pytest.mark.parametrize("layout", ["compact", "random_weights", "as_given"])
+def test_batch_one_step_error(cuda, O, layout):
+    """One step of every network from an identical state.  CSR networks run in the compact
+    layout (16-bit local columns, V_dend staged in shared memory, one scalar weight), with
+    random per-edge weights (compact columns, weight array), or as given (32-bit columns)."""
     nets = _nets(_mixed_specs())
+    if layout == "random_weights":
+        for b in nets:
+            if b["kind"] == "csr":
+                u = inputs.uniform(inputs.stream_seed(b["n"], "edge_w"), len(b["w"]), 0.5, 1.5)
+                b["w"] = (b["w"] * u).astype(np.float32)
     S0, pul = _batch_inputs(O, nets)
-    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0)
+    flags = ion.FLAG_KAHAN | (ion.FLAG_CSR_AS_GIVEN if layout == "as_given" else 0)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=flags)
     try:
         ion.ion_step(h, 1)
         got = ion.ion_read_state(h, S0.shape[1])

@@ -393,12 +393,14 @@ def test_csr_shared_memory_staging(torch_cuda, O, n, k, staging):
     assert err.max() <= STEP_RTOL
 
 
-@pytest.mark.parametrize("n,k,staging", [(3001, 24, 1), (3001, 24, 2), (70000, 30, 1), (70000, 300, 2)])
+@pytest.mark.parametrize("n,k,staging", [(3001, 48, 1), (3001, 12, 1), (3001, 24, 2), (70000, 40, 1), (70000, 300, 2)])
 @pytest.mark.parametrize("weights", ["uniform", "random", "as_given"])
 def test_csr_compact_layouts(torch_cuda, O, n, k, staging, weights):
-    """The compact CSR layouts (16-bit columns; one scalar for bitwise-equal weights) and
-    the layout as given all reproduce the oracle's step; the handle reports what it
-    streams per edge: 16-bit columns when n <= 65 536 or V_dend is staged in chunks."""
+    """The compact CSR layouts (16-bit columns; one scalar for bitwise-equal weights; with
+    staging, the chunk-major layout streamed by bulk copies) and the layout as given all
+    reproduce the oracle's step; the handle reports what it streams per edge: 16-bit
+    columns when V_dend is staged in chunks, or n <= 65 536 with rows of at least 32
+    edges on average."""
     rp, col = inputs.random_symmetric_csr(n, k, 29)
     g = inputs.junction_weight(0.04, k)
     if weights == "random":
@@ -409,11 +411,17 @@ def test_csr_compact_layouts(torch_cuda, O, n, k, staging, weights):
     tune = dict(csr_staging=staging)
     with ion.Simulation(n, ion.CSR, row_ptr=rp, col=col, w=w, flags=flags, tune=tune) as sim:
         lay = ion.ion_csr_layout(sim.h)
-    assert lay["staged"] == (1 if staging == 2 else 0)
+    if staging == 1:
+        assert lay["staged"] == 0
+    elif weights == "as_given":
+        assert lay["staged"] == 1             # V_dend chunks, row-major CSR
+    else:
+        assert lay["staged"] == 2             # V_dend chunks, chunk-major CSR streamed by bulk copies
     if weights == "as_given":
         assert lay == dict(index_bytes=4, weight_bytes=4, staged=lay["staged"])
     else:
-        assert lay["index_bytes"] == (2 if (n <= 65536 or staging == 2) else 4)
+        deg = len(col) / n
+        assert lay["index_bytes"] == (2 if (staging == 2 or (n <= 65536 and deg >= 32)) else 4)
         assert lay["weight_bytes"] == (0 if weights == "uniform" else 4)
     err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=3, flags=flags, tune=tune)
     assert err.max() <= STEP_RTOL, err.max(axis=1)

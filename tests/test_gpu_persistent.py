@@ -35,7 +35,7 @@ def test_persistent_full_work_bitwise_equals_step_launches(cuda, O):
     cfg = inputs.config("c2")
     S0 = initial_state(O, cfg)
     a, la = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN, chunks=3)
-    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_NO_HALF, chunks=3)
+    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT, chunks=3)
     np.testing.assert_array_equal(a, b)
     assert lb < la / 10        # one launch (+ one counter advance) per ion_step call
 
@@ -45,7 +45,7 @@ def test_persistent_half_work_matches_step_launches(cuda, O):
     cfg = inputs.config("c2")
     S0 = initial_state(O, cfg)
     a, _ = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN, chunks=3)
-    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT, chunks=3)
+    b, lb = _run(cfg["n"], cfg["g"], S0, 300, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK, chunks=3)
     assert np.abs(a[:3] - b[:3]).max() <= 1e-3
     assert lb == 6
 
@@ -63,8 +63,8 @@ def test_half_work_one_step_matches_oracle(cuda, O, n, tune):
     Sw, _ = O.run(S0.astype(np.float64), 20, kind=O.DENSE, g=g, threads=max(1, O.max_threads()))
     Sw32 = Sw.astype(np.float32)
     ref, _ = O.run(Sw32.astype(np.float64), 1, kind=O.DENSE, g=g, threads=max(1, O.max_threads()))
-    with ion.Simulation(n, ion.DENSE_UNIFORM, g=g, init_state=Sw32, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
-                        tune=tune) as sim:
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=g, init_state=Sw32,
+                        flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK, tune=tune) as sim:
         sim.step(1)
         got = sim.state()
     err = step_rel_err(got, ref, g * sum_abs_dv(Sw32[0]))
@@ -119,7 +119,8 @@ def test_grid_barrier_timeout_is_reported_not_hung(cuda, O):
 def test_half_work_barrier_timeout_is_reported(cuda, O):
     n = 4096        # several CTAs: the half-work kernel, two bounded barriers per step
     S0 = O.default_state(n).astype(np.float32)
-    with ion.Simulation(n, ion.DENSE_UNIFORM, g=0.001, init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=0.001, init_state=S0,
+                        flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK,
                         barrier_timeout_ns=1_000_000, debug_delay_ns=200_000_000) as sim:
         sim.step(5)
         with pytest.raises(ion.IonError) as ei:

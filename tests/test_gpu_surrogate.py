@@ -25,7 +25,7 @@ def cuda():
 
 @pytest.fixture(scope="module")
 def trained(cuda):
-    w, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=30, batch=2048, lr=2e-3, seed=7, v_lo=-100.0,
+    w, loss = ion.ion_surrogate_train(n_samples=1 << 20, epochs=100, batch=2048, lr=2e-3, seed=7, v_lo=-100.0,
                                       v_hi=50.0, ca_lo=CA_RANGE[0], ca_hi=CA_RANGE[1])
     print(f"surrogate training: final normalised loss {loss:.3e}")
     return w, loss
@@ -114,9 +114,9 @@ def test_learned_rates_subthreshold(trained, O):
 
 
 def test_learned_rates_spiking(trained, O):
-    """Every cell pulsed at 50-60 ms: both methods fire a burst in every sampled cell; the
-    spike counts and times are printed (the surrogate changes the model, it is not a
-    rounding error)."""
+    """Every cell pulsed at 50-60 ms: both methods fire a burst in every sampled cell, with
+    the same number of spikes in most cells and spike times within about 1 ms (the
+    surrogate changes the model, it is not a rounding error)."""
     w, _ = trained
     n = 4096
     te, ts, Ss = _learned_vs_exact(w, O, inputs.pulse_windows(np.arange(n), [(50.0, 60.0)], 6.0))
@@ -132,3 +132,7 @@ def test_learned_rates_spiking(trained, O):
           f"|dt| max {first.max() if len(first) else -1} mean {first.mean() if len(first) else -1:.2f} steps, "
           f"matched |dt| max {dstep.max() if len(dstep) else 0} steps")
     assert all(len(a) >= 1 for a in se) and all(len(b) >= 1 for b in ss)    # every sampled cell fires
+    # the trained network keeps the burst: the same spike count in most cells, spike times
+    # within about a millisecond (20 steps) on average
+    assert sum(same) >= 48, sum(same)
+    assert len(dstep) and dstep.mean() <= 20.0, dstep.mean() if len(dstep) else None
