@@ -253,6 +253,38 @@ void or_gj_csr(int n, const int32_t *row_ptr, const int32_t *col, const double *
     (void)threads;
 }
 
+/* ---- simplified gap junctions (SGJ use case, Sec. 2.3.2) -------------------------
+ * The paper replaces the junction kinetics by simple weighted accumulators (4 operations
+ * per connection).  Read as a linear junction: each connection contributes w (V_i - V_j),
+ * the small-dV limit of the RGJ term (0.8 + 0.2 = 1). */
+
+/* dense uniform all-to-all: Ic_i = g * sum_{j=0}^{n-1} (V_i - V_j), j ascending */
+void or_gj_dense_sgj(int n, const double *vd, double g, double *ic, int threads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += vd[i] - vd[j];
+        ic[i] = g * acc;
+    }
+    (void)threads;
+}
+
+/* CSR: Ic_i = sum_{e in row i} w_e * (V_i - V_{col_e}), edges in stored order */
+void or_gj_csr_sgj(int n, const int32_t *row_ptr, const int32_t *col, const double *w,
+                   const double *vd, double *ic, int threads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int32_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) acc += w[e] * (vd[i] - vd[col[e]]);
+        ic[i] = acc;
+    }
+    (void)threads;
+}
+
 /* ---- cell update (explicit Euler, all right-hand sides from step t) -------------- */
 
 static void cell_step_one(int n, int i, const double *P, double dt, const double *S,
@@ -333,7 +365,8 @@ void or_cell_step(int n, const double *P, double dt, const double *S, const doub
 
 /* ---- whole run -------------------------------------------------------------------
  * kind 0: dense uniform all-to-all with weight g.  kind 1: CSR (row_ptr, col, w).
- * kind 2: no gap junctions (every cell independent).
+ * kind 2: no gap junctions (every cell independent).  kinds 3 and 4: as 0 and 1 with the
+ * simplified (linear) junctions of the SGJ use case.
  * Evoked input at absolute step t (t0 <= t < t0 + n_steps), cell i:
  *   iapp_dense != NULL: iapp_dense[(t - t0) * n + i];
  *   else the sum of amp[p] over pulses p with cell[p] == i and t_begin[p] <= t < t_end[p].
@@ -359,6 +392,8 @@ int or_run(int n, int kind, double g, const int32_t *row_ptr, const int32_t *col
         memcpy(vd, &S[OF_VDEND * n], sizeof(double) * (size_t)n);
         if (kind == 0) or_gj_dense(n, vd, g, ic, threads);
         else if (kind == 1) or_gj_csr(n, row_ptr, col, w, vd, ic, threads);
+        else if (kind == 3) or_gj_dense_sgj(n, vd, g, ic, threads);
+        else if (kind == 4) or_gj_csr_sgj(n, row_ptr, col, w, vd, ic, threads);
         else memset(ic, 0, sizeof(double) * (size_t)n);
         if (iapp_dense) {
             for (int i = 0; i < n; ++i) iapp[i] = (double)iapp_dense[(size_t)st * (size_t)n + (size_t)i];

@@ -36,7 +36,7 @@ PARAMS = ("g_int", "p1", "p2", "g_CaH", "g_KCa", "g_h", "g_ld", "g_CaL", "g_Na_s
           "V_h", "V_L", "C_m", "ca_in", "ca_out", "V_0", "Ca_0")
 P = {name: i for i, name in enumerate(PARAMS)}
 
-DENSE, CSR, NOGJ = 0, 1, 2
+DENSE, CSR, NOGJ, DENSE_SGJ, CSR_SGJ = 0, 1, 2, 3, 4   # SGJ: linear junctions (Sec. 2.3.2)
 DT_MS = 0.05  # Sec. 2.2: delta = 50 us
 
 
@@ -69,6 +69,8 @@ def lib():
             L.or_default_state.argtypes = [ctypes.c_int, dp, dp]
             L.or_gj_dense.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int]
             L.or_gj_csr.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_int]
+            L.or_gj_dense_sgj.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int]
+            L.or_gj_csr_sgj.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_int]
             L.or_cell_step.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
             L.or_run.restype = ctypes.c_int
             L.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, ip, dp, dp,
@@ -138,6 +140,25 @@ def gj_csr(row_ptr, col, w, vd, threads: int = 1) -> np.ndarray:
     return ic
 
 
+def gj_dense_sgj(vd, g: float, threads: int = 1) -> np.ndarray:
+    """SGJ use case: Ic_i = g * sum_j (V_i - V_j)."""
+    vd = np.ascontiguousarray(vd, np.float64)
+    ic = np.zeros_like(vd)
+    lib().or_gj_dense_sgj(len(vd), _d(vd), float(g), _d(ic), int(threads))
+    return ic
+
+
+def gj_csr_sgj(row_ptr, col, w, vd, threads: int = 1) -> np.ndarray:
+    """SGJ use case: Ic_i = sum over row i of w_e (V_i - V_col)."""
+    row_ptr = np.ascontiguousarray(row_ptr, np.int32)
+    col = np.ascontiguousarray(col, np.int32)
+    w = np.ascontiguousarray(w, np.float64)
+    vd = np.ascontiguousarray(vd, np.float64)
+    ic = np.zeros_like(vd)
+    lib().or_gj_csr_sgj(len(vd), _i(row_ptr), _i(col), _d(w), _d(vd), _d(ic), int(threads))
+    return ic
+
+
 def cell_step(S, ic=None, iapp=None, model=None, dt: float = DT_MS, threads: int = 1) -> np.ndarray:
     """One explicit-Euler cell update of every cell, with the gap current given."""
     S = np.ascontiguousarray(S, np.float64)
@@ -161,7 +182,7 @@ def run(S0, n_steps: int, kind: int = DENSE, g: float = 0.0, row_ptr=None, col=N
     S = np.array(S0, np.float64, order="C", copy=True)
     n = S.shape[1]
     model = model_default() if model is None else np.ascontiguousarray(model, np.float64)
-    if kind == CSR:
+    if kind in (CSR, CSR_SGJ):
         row_ptr = np.ascontiguousarray(row_ptr, np.int32)
         col = np.ascontiguousarray(col, np.int32)
         w = np.ascontiguousarray(w, np.float64)

@@ -344,3 +344,52 @@ def test_validation_experiment_complex_spike_in_every_cell(O):
     assert all(len(s) >= 2 for s in sp)                     # a burst: several spikes per cell
     assert all(np.array_equal(s, sp[0]) for s in sp)        # all cells in step
     assert sp[0][0] >= 2000                                  # not before the pulse onset
+
+
+# ---- simplified gap junctions (SGJ use case, Sec. 2.3.2): w (V_i - V_j) per connection
+
+def test_sgj_two_cells_by_hand(O):
+    ic = O.gj_dense_sgj(np.array([-60.0, -50.0]), 0.1)
+    np.testing.assert_allclose(ic, [-1.0, 1.0], rtol=0, atol=1e-12)
+
+
+def test_sgj_dense_closed_form_and_zero_sum(O):
+    rng = np.random.default_rng(3)
+    vd = rng.uniform(-70, -40, 257)
+    g = 0.013
+    ic = O.gj_dense_sgj(vd, g)
+    np.testing.assert_allclose(ic, g * (len(vd) * vd - vd.sum()), rtol=0, atol=1e-9)
+    assert abs(ic.sum()) <= 1e-9 * g * np.abs(vd).sum() * len(vd)
+
+
+def test_sgj_is_the_small_dv_limit_of_rgj(O):
+    """The RGJ term (0.8 e^{-dV^2/100} + 0.2) dV tends to dV: for |dV| <= 1e-3 mV the two
+    junction forms agree to 1e-7 relative (the next term is 0.008 dV^3)."""
+    rng = np.random.default_rng(4)
+    vd = -60.0 + rng.uniform(-1e-3, 1e-3, 64)
+    a = O.gj_dense(vd, 0.02)
+    b = O.gj_dense_sgj(vd, 0.02)
+    assert np.abs(a - b).max() <= 1e-7 * np.abs(b).max()
+
+
+def test_sgj_csr_complete_graph_equals_dense_and_conserves(O):
+    n = 40
+    rp = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.int32)
+    col = np.array([j for i in range(n) for j in range(n) if j != i], np.int32)
+    vd = np.random.default_rng(5).uniform(-65, -45, n)
+    a = O.gj_csr_sgj(rp, col, np.full(len(col), 0.03), vd)
+    np.testing.assert_allclose(a, O.gj_dense_sgj(vd, 0.03), rtol=0, atol=1e-12)
+    rp2, col2 = inputs.random_symmetric_csr(500, 12, 6)
+    vd2 = np.random.default_rng(6).uniform(-65, -45, 500)
+    ic = O.gj_csr_sgj(rp2, col2, np.full(len(col2), 0.05), vd2)
+    assert abs(ic.sum()) <= 1e-10 * np.abs(ic).sum()
+
+
+def test_sgj_run_uses_the_linear_junction(O):
+    """One step of kind DENSE_SGJ equals the cell update fed with the SGJ current."""
+    n = 30
+    S = O.default_state(n)
+    S[O.F["V_dend"]] += np.linspace(-5, 5, n)
+    ref = O.cell_step(S, ic=O.gj_dense_sgj(S[O.F["V_dend"]], 0.02))
+    got, _ = O.run(S, 1, kind=O.DENSE_SGJ, g=0.02)
+    np.testing.assert_array_equal(got, ref)
