@@ -253,6 +253,20 @@ void or_gj_csr(int n, const int32_t *row_ptr, const int32_t *col, const double *
     (void)threads;
 }
 
+/* dense N x N weight matrix (row-major, the programmed connectivity of Sec. 2.3 with every
+ * pair stored): Ic_i = sum_{j=0}^{n-1} W[i][j] * term(V_i - V_j), j ascending */
+void or_gj_matrix(int n, const double *W, const double *vd, double *ic, int threads) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
+#endif
+    for (int i = 0; i < n; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < n; ++j) acc += W[(size_t)i * (size_t)n + (size_t)j] * gj_term(vd[i] - vd[j]);
+        ic[i] = acc;
+    }
+    (void)threads;
+}
+
 /* ---- simplified gap junctions (SGJ use case, Sec. 2.3.2) -------------------------
  * The paper replaces the junction kinetics by simple weighted accumulators (4 operations
  * per connection).  Read as a linear junction: each connection contributes w (V_i - V_j),
@@ -366,7 +380,8 @@ void or_cell_step(int n, const double *P, double dt, const double *S, const doub
 /* ---- whole run -------------------------------------------------------------------
  * kind 0: dense uniform all-to-all with weight g.  kind 1: CSR (row_ptr, col, w).
  * kind 2: no gap junctions (every cell independent).  kinds 3 and 4: as 0 and 1 with the
- * simplified (linear) junctions of the SGJ use case.
+ * simplified (linear) junctions of the SGJ use case.  kind 5: dense N x N weight matrix
+ * (w holds n * n row-major weights).
  * Evoked input at absolute step t (t0 <= t < t0 + n_steps), cell i:
  *   iapp_dense != NULL: iapp_dense[(t - t0) * n + i];
  *   else the sum of amp[p] over pulses p with cell[p] == i and t_begin[p] <= t < t_end[p].
@@ -394,6 +409,7 @@ int or_run(int n, int kind, double g, const int32_t *row_ptr, const int32_t *col
         else if (kind == 1) or_gj_csr(n, row_ptr, col, w, vd, ic, threads);
         else if (kind == 3) or_gj_dense_sgj(n, vd, g, ic, threads);
         else if (kind == 4) or_gj_csr_sgj(n, row_ptr, col, w, vd, ic, threads);
+        else if (kind == 5) or_gj_matrix(n, w, vd, ic, threads);
         else memset(ic, 0, sizeof(double) * (size_t)n);
         if (iapp_dense) {
             for (int i = 0; i < n; ++i) iapp[i] = (double)iapp_dense[(size_t)st * (size_t)n + (size_t)i];

@@ -36,7 +36,7 @@ PARAMS = ("g_int", "p1", "p2", "g_CaH", "g_KCa", "g_h", "g_ld", "g_CaL", "g_Na_s
           "V_h", "V_L", "C_m", "ca_in", "ca_out", "V_0", "Ca_0")
 P = {name: i for i, name in enumerate(PARAMS)}
 
-DENSE, CSR, NOGJ, DENSE_SGJ, CSR_SGJ = 0, 1, 2, 3, 4   # SGJ: linear junctions (Sec. 2.3.2)
+DENSE, CSR, NOGJ, DENSE_SGJ, CSR_SGJ, MATRIX = 0, 1, 2, 3, 4, 5   # SGJ: linear junctions (Sec. 2.3.2)
 DT_MS = 0.05  # Sec. 2.2: delta = 50 us
 
 
@@ -70,6 +70,7 @@ def lib():
             L.or_gj_dense.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int]
             L.or_gj_csr.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_int]
             L.or_gj_dense_sgj.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int]
+            L.or_gj_matrix.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
             L.or_gj_csr_sgj.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_int]
             L.or_cell_step.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
             L.or_run.restype = ctypes.c_int
@@ -140,6 +141,16 @@ def gj_csr(row_ptr, col, w, vd, threads: int = 1) -> np.ndarray:
     return ic
 
 
+def gj_matrix(W, vd, threads: int = 1) -> np.ndarray:
+    """Dense N x N weights: Ic_i = sum_j W[i, j] (0.8 e^{-dV^2/100} + 0.2) dV."""
+    vd = np.ascontiguousarray(vd, np.float64)
+    W = np.ascontiguousarray(W, np.float64)
+    assert W.shape == (len(vd), len(vd))
+    ic = np.zeros_like(vd)
+    lib().or_gj_matrix(len(vd), _d(W), _d(vd), _d(ic), int(threads))
+    return ic
+
+
 def gj_dense_sgj(vd, g: float, threads: int = 1) -> np.ndarray:
     """SGJ use case: Ic_i = g * sum_j (V_i - V_j)."""
     vd = np.ascontiguousarray(vd, np.float64)
@@ -182,6 +193,9 @@ def run(S0, n_steps: int, kind: int = DENSE, g: float = 0.0, row_ptr=None, col=N
     S = np.array(S0, np.float64, order="C", copy=True)
     n = S.shape[1]
     model = model_default() if model is None else np.ascontiguousarray(model, np.float64)
+    if kind == MATRIX:
+        w = np.ascontiguousarray(w, np.float64)
+        assert w.shape == (n, n)
     if kind in (CSR, CSR_SGJ):
         row_ptr = np.ascontiguousarray(row_ptr, np.int32)
         col = np.ascontiguousarray(col, np.int32)

@@ -393,3 +393,35 @@ def test_sgj_run_uses_the_linear_junction(O):
     ref = O.cell_step(S, ic=O.gj_dense_sgj(S[O.F["V_dend"]], 0.02))
     got, _ = O.run(S, 1, kind=O.DENSE_SGJ, g=0.02)
     np.testing.assert_array_equal(got, ref)
+
+
+# ---- dense N x N weight matrix (programmed connectivity with every pair stored, Sec. 2.3)
+
+def test_matrix_uniform_equals_dense_uniform(O):
+    vd = np.random.default_rng(7).uniform(-70, -40, 123)
+    W = np.full((123, 123), 0.017)
+    np.testing.assert_allclose(O.gj_matrix(W, vd), O.gj_dense(vd, 0.017), rtol=1e-13, atol=1e-13)
+
+
+def test_matrix_equals_weighted_complete_csr(O):
+    """Any matrix equals the CSR of the complete graph with the same off-diagonal weights
+    (the diagonal pair contributes exactly zero whatever its weight)."""
+    n = 60
+    rng = np.random.default_rng(8)
+    W = rng.uniform(0.0, 0.1, (n, n))
+    vd = rng.uniform(-70, -40, n)
+    rp = np.arange(0, n * (n - 1) + 1, n - 1, dtype=np.int32)
+    col = np.array([j for i in range(n) for j in range(n) if j != i], np.int32)
+    w = np.array([W[i, j] for i in range(n) for j in range(n) if j != i])
+    np.testing.assert_allclose(O.gj_matrix(W, vd), O.gj_csr(rp, col, w, vd), rtol=1e-13, atol=1e-13)
+
+
+def test_matrix_two_cells_by_hand_and_symmetric_conservation(O):
+    W = np.array([[5.0, 0.3], [0.7, 9.0]])
+    vd = np.array([-60.0, -50.0])
+    t = (0.8 * np.exp(-1.0) + 0.2) * 10.0        # term(+10); term(-10) = -t
+    np.testing.assert_allclose(O.gj_matrix(W, vd), [-0.3 * t, 0.7 * t], rtol=1e-14)
+    rng = np.random.default_rng(9)
+    A = rng.uniform(0, 0.05, (80, 80))
+    ic = O.gj_matrix(A + A.T, rng.uniform(-70, -40, 80))
+    assert abs(ic.sum()) <= 1e-12 * np.abs(ic).sum()
