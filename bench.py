@@ -9,7 +9,9 @@ Metric: cell-timesteps/s (and gap-junction pair evaluations/s, N^2 per time step
 1 s; c3_k10 / c3_k100 / c3_k1000: 65 536 cells with random symmetric CSR connectivity;
 c4: 256 uneven networks in one batch; c5: the k = 100 network for 1 s with the learned
 rate-function surrogate against the exact FP32 method; k3: the cell update alone on 2^22
-uncoupled cells, with a sweep of sizes from 2^16).
+uncoupled cells, with a sweep of sizes from 2^16; c2_sgj: the 8192-cell network with the
+simplified linear junctions of the SGJ use case; c2_matrix: 8192 cells with an N x N
+weight matrix streamed from HBM every step).
 `--impl reference` times the FP64 CPU oracle instead (a bounded sample, all host cores).
 Prints one JSON line.
 """
@@ -40,6 +42,8 @@ WORKLOADS = {
     "c4": dict(name="c4_batch_256_nets_logU32-4096_half_dense_100ms", cfg="c4", steps=2000),
     "c5": dict(name="c5_surrogate_csr_65536_k100_1s", cfg="c3", k=100, steps=20000),
     "k3": dict(name="k3_cell_update_ngj_4194304_20ms", cfg="k3", n=1 << 22, steps=400),
+    "c2_sgj": dict(name="c2_sgj_dense_8192_linearGJ_200ms", cfg="c2", steps=4000, sgj=True),
+    "c2_matrix": dict(name="c2_matrix_dense_8192_NxN_weights_100ms", cfg="c2_matrix", steps=2000),
 }
 K3_SWEEP = (1 << 16, 1 << 18, 1 << 20, 1 << 22)
 
@@ -253,9 +257,12 @@ def cpu_baseline(key, sample_steps):
         S = O.default_state(b["n"])
         S[O.F["V_dend"]] += b["jitter"]
         S = S.astype(np.float32).astype(np.float64)
-        kind = {"dense": O.DENSE, "csr": O.CSR, "ngj": O.NOGJ}[b["kind"]]
+        kind = {"dense": O.DENSE, "csr": O.CSR, "ngj": O.NOGJ, "matrix": O.MATRIX}[b["kind"]]
+        if WORKLOADS[key].get("sgj"):
+            kind = {O.DENSE: O.DENSE_SGJ, O.CSR: O.CSR_SGJ}[kind]
+        wt = b.get("W") if b["kind"] == "matrix" else b.get("w")
         kw = dict(kind=kind, g=b.get("g", 0.0), row_ptr=b.get("row_ptr"), col=b.get("col"),
-                  w=None if b.get("w") is None else b["w"].astype(np.float64), threads=threads)
+                  w=None if wt is None else wt.astype(np.float64), threads=threads)
         runs.append((S, kw))
     O.run(runs[0][0], 1, **runs[0][1])        # warm caches and the thread pool
     t0 = time.perf_counter()
@@ -269,7 +276,7 @@ def cpu_baseline(key, sample_steps):
 
 
 def reference_sample_steps(key):
-    return {"c2": 8, "c1": 2000, "c4": 3, "k3": 3}.get(key, 20)
+    return {"c2": 8, "c1": 2000, "c4": 3, "k3": 3, "c2_matrix": 4}.get(key, 20)
 
 
 def run_reference(args, rank):
@@ -343,6 +350,8 @@ def main():
 
     def make_sim(flags):
         nonlocal tune_table
+        if wl.get("sgj"):
+            flags |= ion.FLAG_SGJ
         if batch:
             specs = [dict(n=b["n"], kind=ion.DENSE_UNIFORM, g=b["g"]) if b["kind"] == "dense" else
                      dict(n=b["n"], kind=ion.CSR, row_ptr=b["row_ptr"], col=b["col"], w=b["w"]) for b in cfg["nets"]]
@@ -354,6 +363,8 @@ def main():
             return sim
         if ngj:
             kind, kw = ion.NO_GJ, {}
+        elif cfg["kind"] == "matrix":
+            kind, kw = ion.DENSE_MATRIX, dict(w=cfg["W"])
         elif dense:
             kind, kw = ion.DENSE_UNIFORM, dict(g=cfg["g"])
         else:
@@ -363,6 +374,8 @@ def main():
         sim = ion.Simulation(n, kind, init_state=S0, stream=stream, graph_steps=100, flags=flags, **kw)
         if cfg.get("pulses") is not None:
             sim.set_input(cfg["pulses"])
+        if not (flags & (ion.FLAG_PERSISTENT | ion.FLAG_SURROGATE)) and kind in (ion.DENSE_UNIFORM, ion.CSR):
+            tune_table = ion.ion_autotune(sim.h, 20)    # launch shape timed on this network (state restored)
         return sim
 
     def reset(sim):
@@ -394,10 +407,10 @@ def main():
         launches = sim.launches - launches0
         ms = sum(a.elapsed_time(b) for a, b in ev)
         sim.sync()                                      # the run stayed finite
-        return sim, ms, launches, ck
+        return sim, ms, launches, ck, tune_table
 
     cand = [("graph", ion.FLAG_KAHAN)]
-    if dense:
+    if dense and not wl.get("sgj"):
         cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
         if n > 144:   # multi-CTA networks: the half-work pass as well as the full pass
             cand.append(("persistent_half", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK))
@@ -409,8 +422,9 @@ def main():
         cand = [("exact", ion.FLAG_KAHAN), ("surrogate", ion.FLAG_KAHAN | ion.FLAG_SURROGATE)]
     variants = {}
     for name, flags in cand:
-        sim_v, ms_v, l_v, ck_v = measure(flags)
-        variants[name] = dict(sim=sim_v, ms=ms_v, launches=l_v, clocks=ck_v)
+        tune_table = None
+        sim_v, ms_v, l_v, ck_v, tt_v = measure(flags)
+        variants[name] = dict(sim=sim_v, ms=ms_v, launches=l_v, clocks=ck_v, tune=tt_v)
     best = min(variants, key=lambda k: variants[k]["ms"])
     if key == "c5":   # the line reports the surrogate; the exact method is its comparison
         best = "surrogate"
@@ -451,6 +465,29 @@ def main():
         extra = {"pair_evals_per_s": sum(b["n"] ** 2 for b in cfg["nets"] if b["kind"] == "dense") / per_step_s,
                  "edges_per_s": sum(len(b["col"]) for b in cfg["nets"] if b["kind"] == "csr") / per_step_s,
                  "autotuned": tune_table, "n_networks": len(cfg["nets"])}
+    elif cfg["kind"] == "matrix":
+        # HBM: the padded weight matrix (4 B per stored pair) streams every step, plus the
+        # cell state (132 B per cell)
+        n_pad = (n + 255) // 256 * 256
+        bytes_step = 4 * n * n_pad + 132 * n
+        achieved = bytes_step / per_step_s / 1e9
+        peak = hbm_peak()
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "matrix_step_kernel", "algorithmic_bytes_per_timestep": bytes_step,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6}
+        extra = {"pair_evals_per_s": value * n}
+    elif dense and wl.get("sgj"):
+        # linear junctions: O(N) per step (the sum of V_dend, then each cell's update): the
+        # state (132 B per cell) and one read of V_dend by the partial sums
+        bytes_step = 132 * n + 4 * n
+        achieved = bytes_step / per_step_s / 1e9
+        peak = hbm_peak()
+        roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                "traffic": None, "kernel": "sgj_dense_update_kernel (+ sgj_partial_kernel)",
+                "algorithmic_bytes_per_timestep": bytes_step, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                "us_per_timestep": per_step_s * 1e6,
+                "note": "latency-bound: two short launches per step on an L2-resident state"}
+        extra = {"pair_evals_per_s": value * n}
     elif dense:
         # SFU-bound: one ex2 per pair evaluation (N^2 per time step); the half-work kernel
         # evaluates each unordered pair once (N^2 / 2 ex2 per time step)
@@ -497,9 +534,7 @@ def main():
         nnz = len(cfg["col"])
         lay = ion.ion_csr_layout(sim.h)
         n_pad = (n + 255) // 256 * 256
-        if lay["staged"] == 2:    # chunk-major: row bounds of every chunk (n + 1 each)
-            ptr_bytes = 4 * (n + 1) * ((n_pad + 16383) // 16384)
-        elif lay["staged"] == 1:  # row-major: row pointers + interior chunk boundaries
+        if lay["staged"]:         # row pointers + interior chunk boundaries
             ptr_bytes = 4 * (n + 1) + 4 * n * ((n_pad + 32767) // 32768 - 1)
         else:
             ptr_bytes = 4 * (n + 1)
@@ -508,7 +543,7 @@ def main():
         peak = hbm_peak()
         roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
                 "traffic": None,
-                "kernel": ["csr_step_kernel", "csr_chunk_step_kernel", "csr_stream_kernel"][lay["staged"]],
+                "kernel": "csr_chunk_step_kernel" if lay["staged"] else "csr_step_kernel",
                 "algorithmic_bytes_per_timestep": bytes_step,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs", "us_per_timestep": per_step_s * 1e6,
                 "note": "working set fits in L2 (129 MB)" if bytes_step < 100e6 else "streams from HBM",
@@ -530,6 +565,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": ck,
         }
+        if variants[best]["tune"] is not None and "autotuned" not in extra:
+            line["autotuned"] = variants[best]["tune"]
         line.update(extra)
     if not args.no_extra:
         # e2e through the public API with pinned host buffers (H2D state in, D2H state out)

@@ -81,7 +81,8 @@ enum ion_param {
 enum ion_net_kind {
     ION_DENSE_UNIFORM = 0, /* all-to-all, one weight g_c for every pair (RGJ, C = 100 %) */
     ION_CSR = 1,           /* CSR weight matrix (RGJ at any density)                     */
-    ION_NO_GJ = 2          /* independent cells (NGJ use case, Sec. 2.3.3)               */
+    ION_NO_GJ = 2,         /* independent cells (NGJ use case, Sec. 2.3.3)               */
+    ION_DENSE_MATRIX = 3   /* all-to-all with an N x N weight matrix (every pair stored)   */
 };
 enum ion_mem { ION_HOST = 0, ION_DEVICE = 1 };
 
@@ -97,8 +98,11 @@ enum ion_flag {
     ION_FLAG_HALF_WORK = 1u << 6,  /* persistent dense with several CTAs: evaluate each unordered
                                       pair once (I_ij = -I_ji), exchanging column sums through
                                       L2 (two bounded barriers per step)                     */
-    ION_FLAG_CSR_AS_GIVEN = 1u << 7 /* CSR: keep 32-bit columns and per-edge weights even when
+    ION_FLAG_CSR_AS_GIVEN = 1u << 7, /* CSR: keep 32-bit columns and per-edge weights even when
                                       a compact layout applies (see ion_csr_layout)         */
+    ION_FLAG_SGJ = 1u << 8         /* SGJ use case (Sec. 2.3.2): each connection contributes
+                                      w (V_i - V_j) instead of the RGJ term.  Dense or CSR;
+                                      not with PERSISTENT, SURROGATE, SPLIT or batches      */
 };
 
 typedef struct {
@@ -106,7 +110,10 @@ typedef struct {
     int32_t kind;    /* enum ion_net_kind */
 } ion_net;
 
-/* Connectivity.  Dense: g_c is the weight of every pair.  CSR: row_ptr[n+1] (int32,
+/* Connectivity.  Dense: g_c is the weight of every pair.  Dense matrix: weight[n * n]
+ * (row-major, W[i][j] weighs the current into cell i from cell j; the diagonal pair
+ * contributes zero whatever its weight); row_ptr/col_idx unused; the matrix is copied into
+ * the handle (padded rows), host matrices are checked to be finite.  CSR: row_ptr[n+1] (int32,
  * row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz), col_idx[nnz] in [0, n), strictly
  * ascending within a row, no self loops, pattern symmetric; weight[nnz] (may be NULL:
  * every weight is g_c).  mem says where the three arrays live; ION_DEVICE arrays are
@@ -256,9 +263,7 @@ ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
  *                 its chunk fits in 16 bits), or the network has at most 65 536 cells and a
  *                 mean degree of at least 32; else 4;
  *   *weight_bytes 0 when every weight is bitwise equal (one scalar is kept), else 4;
- *   *staged       1 when V_dend is staged in shared memory chunk by chunk (row-major CSR),
- *                 2 when, in addition, the CSR is kept chunk-major and streamed by bulk
- *                 copies (16-bit columns, compact layout), else 0.
+ *   *staged       1 when V_dend is staged in shared memory chunk by chunk, else 0.
  * Both compactions are exact: the kernels evaluate the same edges with the same values.
  * ION_FLAG_CSR_AS_GIVEN turns them off.  Dense / NGJ handles report 0, 0, 0.  Any output
  * pointer may be NULL. */

@@ -278,15 +278,6 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
     if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr) return ION_OK;
-    // compact layout: the chunk-major CSR streamed by bulk copies, where it applies
-    if (s->d_col16) {
-        const ion_status st = s->stream_ns > 0 ? ION_OK : ion_setup_csr_stream(s);
-        if (st != ION_OK) return st;
-        if (s->stream_ns > 0) {
-            s->csr_staged = 2;
-            return ION_OK;
-        }
-    }
     s->n_chunks = (s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK;
     int rows = (s->n + s->sms - 1) / s->sms;
     if (rows > 1024) rows = 1024;
@@ -300,13 +291,20 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
         if (e == cudaSuccess) e = launch_csr_chunk_bounds(s->d_rowptr, s->d_col, s->n, s->n_chunks, s->d_mid, s->st);
         if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
     }
+    const ion_status st = ion_prepare_csr_chunk(s);
+    if (st != ION_OK) return st;
+    s->csr_staged = 1;
+    return ION_OK;
+}
+
+// Allow the staged kernel of the current lanes-per-row choice its dynamic shared memory.
+ion_status ion_prepare_csr_chunk(ion_sim *s) {
     CsrArgs probe{};
     probe.c.n = s->n;
     probe.c.n_pad = s->n_pad;
     ion_csr_fill(s, probe, true);
     cudaError_t e = launch_csr_chunk_step(probe, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, true, s->st);
     if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
-    s->csr_staged = 1;
     return ION_OK;
 }
 
@@ -326,12 +324,11 @@ void ion_sim_free_device(ion_sim *s) {
     }
     cudaFree(s->d_col16);
     s->d_col16 = nullptr;
-    cudaFree(s->d_crp);
-    cudaFree(s->d_ccol);
-    cudaFree(s->d_cw);
-    s->d_crp = nullptr;
-    s->d_ccol = nullptr;
-    s->d_cw = nullptr;
+    cudaFree(s->d_sgj);
+    s->d_sgj = nullptr;
+    cudaFree(s->d_W);
+    s->d_W = nullptr;
+
     cudaFree(s->d_poff);
     cudaFree(s->d_pbeg);
     cudaFree(s->d_pend);
@@ -351,7 +348,8 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     if (!net || !params) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: NULL net/params");
     if (net->n_cells < 1 || net->n_cells > (1 << 28))
         return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: n_cells = %d out of range", net->n_cells);
-    if (net->kind != ION_DENSE_UNIFORM && net->kind != ION_CSR && net->kind != ION_NO_GJ)
+    if (net->kind != ION_DENSE_UNIFORM && net->kind != ION_CSR && net->kind != ION_NO_GJ &&
+        net->kind != ION_DENSE_MATRIX)
         return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: unknown network kind %d", net->kind);
     if (net->kind != ION_NO_GJ && !conn) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: NULL conn");
     if (conn && conn->mem != ION_HOST && conn->mem != ION_DEVICE)
@@ -362,6 +360,19 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         ion_status st = ion_validate_csr(net->n_cells, conn);
         if (st != ION_OK) return st;
     }
+    if (net->kind == ION_DENSE_MATRIX) {
+        if (!conn->weight) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dense matrix without weights");
+        if (params->flags & (ION_FLAG_PERSISTENT | ION_FLAG_SURROGATE | ION_FLAG_SPLIT | ION_FLAG_SGJ))
+            return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create: flags not supported with a dense matrix");
+        if (conn->mem == ION_HOST)
+            for (int64_t q = 0; q < (int64_t)net->n_cells * net->n_cells; ++q)
+                if (!std::isfinite(conn->weight[q]))
+                    return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: matrix weight %lld not finite", (long long)q);
+    }
+    if ((params->flags & ION_FLAG_SGJ) &&
+        (net->kind == ION_NO_GJ || (params->flags & (ION_FLAG_PERSISTENT | ION_FLAG_SURROGATE | ION_FLAG_SPLIT))))
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create: ION_FLAG_SGJ needs a dense or CSR network "
+                        "without PERSISTENT, SURROGATE or SPLIT");
     const double dt = params->dt_ms > 0 ? params->dt_ms : 0.05;
     if (!std::isfinite(dt) || dt > 1.0) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: dt_ms out of range");
     ion_model m;
@@ -444,6 +455,16 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         s->dense_GJ = GJ;
         e = prepare_dense_step(R, W, GJ, s->n_pad);
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: dense setup: %s", cudaGetErrorString(e)));
+    } else if (s->kind == ION_DENSE_MATRIX) {
+        e = cudaMalloc(&s->d_W, (size_t)s->n * s->n_pad * sizeof(float));
+        if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: matrix allocation: %s", cudaGetErrorString(e)));
+        e = cudaMemsetAsync(s->d_W, 0, (size_t)s->n * s->n_pad * sizeof(float), s->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(s->d_W, (size_t)s->n_pad * sizeof(float), conn->weight, (size_t)s->n * sizeof(float),
+                                  (size_t)s->n * sizeof(float), (size_t)s->n,
+                                  conn->mem == ION_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess) e = prepare_matrix_step(s->n_pad);
+        if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: matrix copy: %s", cudaGetErrorString(e)));
     } else if (s->kind == ION_CSR) {
         s->g = conn->g_c;
         s->nnz = conn->nnz;
@@ -497,6 +518,11 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         s->csr_rows = rows;
         const ion_status st3 = ion_setup_csr_staging(s, tu ? tu->csr_staging : 0);
         if (st3 != ION_OK) return fail(st3);
+    }
+    if ((s->flags & ION_FLAG_SGJ) && s->kind == ION_DENSE_UNIFORM) {
+        s->lps = 2;   // partial sums + update
+        e = cudaMalloc(&s->d_sgj, (size_t)sgj_partials(s->n) * sizeof(float));
+        if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
     }
     if ((s->flags & ION_FLAG_SPLIT) && s->kind != ION_NO_GJ) {
         s->lps = 2;
@@ -622,6 +648,30 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
     const StepCommon c = ion_step_common(s, k_off, iapp);
     const bool split = (s->flags & ION_FLAG_SPLIT) != 0;
     cudaError_t e = cudaSuccess;
+    if (s->kind == ION_DENSE_MATRIX) {
+        MatrixArgs a{};
+        a.c = c;
+        a.W = s->d_W;
+        e = launch_matrix_step(a, s->st);
+        s->launches++;
+        return e;
+    }
+    if (s->flags & ION_FLAG_SGJ) {   // linear junctions (SGJ use case)
+        if (s->kind == ION_DENSE_UNIFORM) {
+            e = launch_sgj_dense_step(c, s->g, s->d_sgj, s->st);
+            s->launches += 2;
+        } else {
+            CsrArgs a{};
+            a.c = c;
+            a.row_ptr = s->d_rowptr;
+            a.col = s->d_col;
+            a.w = s->d_w;
+            a.g = s->g;
+            e = launch_sgj_csr_step(a, s->st);
+            s->launches++;
+        }
+        return e;
+    }
     if (s->kind == ION_DENSE_UNIFORM) {
         DenseArgs a{};
         a.c = c;
@@ -644,9 +694,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
         a.fuse = split ? 0 : 1;
         a.ic_out = s->d_ic;
         a.vd_in = nullptr;
-        if (s->csr_staged == 2 && !split)
-            e = launch_csr_stream(s, c, s->st);
-        else if (s->csr_staged == 1 && !split)
+        if (s->csr_staged == 1 && !split)
             e = launch_csr_chunk_step(a, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, false, s->st);
         else
             e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);

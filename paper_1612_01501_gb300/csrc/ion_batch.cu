@@ -417,7 +417,7 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     *out = nullptr;
     if (n_nets < 1 || !nets || !conns || !params)
         return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad arguments");
-    if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_PERSISTENT | ION_FLAG_SPLIT))
+    if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_PERSISTENT | ION_FLAG_SPLIT | ION_FLAG_SGJ))
         return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: flags not supported for batches");
     // validate and lay out
     std::vector<BatchNet> bn((size_t)n_nets);
@@ -688,24 +688,21 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         int b_csw = s->csr_chunk_SW;
         const int sw0 = s->csr_SW;
         for (int staged = 0; staged <= 1 && st == ION_OK; ++staged) {
-            if (staged) {   // the staged layout the handle supports (streamed or row-major)
+            if (staged) {
                 if (ion_setup_csr_staging(s, 2) != ION_OK || s->csr_staged == 0) break;
             } else {
                 s->csr_staged = 0;
             }
             const int mode = s->csr_staged;
-            bool timed_stream = false;
             for (int sw : SWs) {
-                if (mode == 2) {                               // streamed: one warp per row, one shape
-                    if (timed_stream) continue;
-                    timed_stream = true;
-                } else if (sw * 4 < sw0 || sw > sw0 * 4) {
-                    continue;                                  // near the degree-based choice
-                }
+                if (sw * 4 < sw0 || sw > sw0 * 4) continue;   // near the degree-based choice
                 for (int r : rows) {
                     if (staged && r != rows[0]) continue;     // staged: rows per CTA fixed by the SM count
-                    if (staged) s->csr_chunk_SW = sw;
-                    else {
+                    if (staged) {
+                        s->csr_chunk_SW = sw;
+                        st = ion_prepare_csr_chunk(s);
+                        if (st != ION_OK) break;
+                    } else {
                         s->csr_SW = sw;
                         s->csr_rows = r;
                     }
@@ -729,8 +726,8 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         s->csr_rows = brows;
         s->csr_staged = bstaged;
         s->csr_chunk_SW = b_csw;
-        bt.csr_lanes_per_row = bstaged == 2 ? 32 : bstaged ? b_csw : bsw;
-        bt.csr_rows_per_cta = bstaged == 2 ? s->stream_rows : bstaged ? s->csr_chunk_rows : brows;
+        bt.csr_lanes_per_row = bstaged ? b_csw : bsw;
+        bt.csr_rows_per_cta = bstaged ? s->csr_chunk_rows : brows;
         bt.csr_staging = bstaged ? 2 : 1;
     }
     if (s->gexec) {

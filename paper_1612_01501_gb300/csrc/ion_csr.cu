@@ -12,6 +12,8 @@
 // cell work runs on full warps whatever SW is.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "ion_async.cuh"
 #include "ion_csr_core.cuh"
 #include "ion_kernels.cuh"
@@ -263,6 +265,98 @@ cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, 
                                     cudaStream_t st) {
     if (n_chunks <= 1) return cudaSuccess;
     csr_chunk_bounds_kernel<<<(n + 255) / 256, 256, 0, st>>>(row_ptr, col, n, n_chunks, mid);
+    return cudaGetLastError();
+}
+
+// ---- simplified gap junctions (SGJ use case, Sec. 2.3.2) ---------------------------------
+// Each connection contributes w (V_i - V_j) (the small-dV limit of the RGJ term).
+// Dense: Ic_i = g sum_j (V_i - V_j) = g (N (V_i - m) - sum_j (V_j - m)), m = V_dend of cell 0
+// (shifted so nearly equal voltages do not cancel).  Two launches per step: P CTAs write
+// Kahan partial sums of V_j - m over fixed strided ranges, then every CTA of the update
+// sums the P partials in index order and updates its cells (deterministic).
+__global__ void __launch_bounds__(256) sgj_partial_kernel(const StepCommon c, float *part) {
+    __shared__ float red[8];
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    const float m = vcur[0];
+    float s = 0.0f, cc = 0.0f;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c.n; j += (int64_t)gridDim.x * blockDim.x)
+        kahan_add(s, cc, vcur[j] - m);
+    float v = s - cc;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float tot = 0.0f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        part[blockIdx.x] = tot;
+    }
+}
+__global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon c, const float *part, int n_part,
+                                                               float g) {
+    __shared__ float U_sh;
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    float *vnext = vd_next(c, t);
+    if (threadIdx.x == 0) {
+        float s = 0.0f, cc = 0.0f;
+        for (int q = 0; q < n_part; ++q) kahan_add(s, cc, part[q]);
+        U_sh = s - cc;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c.n) return;
+    const float m = vcur[0];
+    const float ic = g * fmaf((float)c.n, vcur[i] - m, -U_sh);
+    const Cell cell = load_cell(c.S, vcur, i);
+    float iapp = pulse_current(c.pulses, i, t);
+    if (c.iapp != nullptr) iapp += c.iapp[i];
+    const CellNext o = cell_step(c.P, cell, ic, iapp);
+    finish_cell(c, t, vnext, i, o);
+}
+cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st) {
+    const int n_part = sgj_partials(c.n);
+    sgj_partial_kernel<<<n_part, 256, 0, st>>>(c, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sgj_dense_update_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, part, n_part, g);
+    return cudaGetLastError();
+}
+int sgj_partials(int n) { return std::min(256, std::max(1, (n + 4095) / 4096)); }
+
+// CSR: eight lanes per row, 32 rows per CTA, then the cell update of the CTA's rows.
+__global__ void __launch_bounds__(256) sgj_csr_step_kernel(const CsrArgs a) {
+    __shared__ float ic_s[32];
+    const StepCommon &c = a.c;
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    float *vnext = vd_next(c, t);
+    const int sub = threadIdx.x >> 3, li = threadIdx.x & 7;
+    const int i = blockIdx.x * 32 + sub;
+    float acc = 0.0f;
+    if (i < c.n) {
+        const float vi = vcur[i];
+        for (int e = a.row_ptr[i] + li; e < a.row_ptr[i + 1]; e += 8) {
+            const float dv = vi - __ldg(vcur + __ldg(a.col + e));
+            acc = a.w != nullptr ? fmaf(__ldg(a.w + e), dv, acc) : acc + dv;
+        }
+    }
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (li == 0) ic_s[sub] = a.w != nullptr ? acc : acc * a.g;
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int r = blockIdx.x * 32 + threadIdx.x;
+    if (r >= c.n) return;
+    const Cell cell = load_cell(c.S, vcur, r);
+    float iapp = pulse_current(c.pulses, r, t);
+    if (c.iapp != nullptr) iapp += c.iapp[r];
+    const CellNext o = cell_step(c.P, cell, ic_s[threadIdx.x], iapp);
+    finish_cell(c, t, vnext, r, o);
+}
+cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st) {
+    sgj_csr_step_kernel<<<(unsigned)((a.c.n + 31) / 32), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -70,33 +70,80 @@ __device__ __forceinline__ float csr_row_sum_smem(const float *vs, int c0, const
     return acc;
 }
 
+// Eight edges of a 16-byte group of 16-bit columns (and their weights).
+template <bool HAS_W, class VJ>
+__device__ __forceinline__ float csr_group16(uint4 q, float4 wa, float4 wb, float vi, VJ vj) {
+    const float v0 = vj(q.x & 0xFFFFu), v1 = vj(q.x >> 16), v2 = vj(q.y & 0xFFFFu), v3 = vj(q.y >> 16);
+    const float v4 = vj(q.z & 0xFFFFu), v5 = vj(q.z >> 16), v6 = vj(q.w & 0xFFFFu), v7 = vj(q.w >> 16);
+    return ((gj_edge(vi, v0, wa.x) + gj_edge(vi, v1, wa.y)) + (gj_edge(vi, v2, wa.z) + gj_edge(vi, v3, wa.w))) +
+           ((gj_edge(vi, v4, wb.x) + gj_edge(vi, v5, wb.y)) + (gj_edge(vi, v6, wb.z) + gj_edge(vi, v7, wb.w)));
+}
+template <bool HAS_W, bool LD_STREAM>
+__device__ __forceinline__ void csr_load16(const uint16_t *__restrict__ col16, const float *__restrict__ w, int e,
+                                           uint4 &q, float4 &wa, float4 &wb) {
+    q = LD_STREAM ? __ldcs(reinterpret_cast<const uint4 *>(col16 + e)) : __ldg(reinterpret_cast<const uint4 *>(col16 + e));
+    wa = wb = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+    if (HAS_W) {
+        wa = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e)) : __ldg(reinterpret_cast<const float4 *>(w + e));
+        wb = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e + 4))
+                       : __ldg(reinterpret_cast<const float4 *>(w + e + 4));
+    }
+}
+
+template <bool LD_STREAM>
+__device__ __forceinline__ uint32_t csr_ld16(const uint16_t *__restrict__ col16, int e) {
+    return LD_STREAM ? (uint32_t)__ldcs(col16 + e) : (uint32_t)__ldg(col16 + e);
+}
+
 // 16-bit column indices: col16[e] holds the low 16 bits of column e (exact when the
-// network has at most 65 536 cells; chunk-relative below).  The body of a row is read
-// eight edges per lane with one 16-byte load of indices (and two of weights); vj maps a
-// 16-bit index to V_dend of that column.  LD_STREAM: the indices are read once per step
-// (evict-first), else through the read-only cache.
+// network has at most 65 536 cells; chunk-relative below).  A row is read as an unaligned
+// head (< 8 edges), a body of 16-byte groups of eight edges and a tail (< 8 edges).  With
+// eight or more lanes per row the head and tail take one load per lane, and each lane
+// issues them together with its first two body groups before using any, so a row costs
+// one memory latency rather than one per part (rows of up to 16 x SW body edges are then
+// done in one round).  vj maps a 16-bit index to V_dend of that column.  LD_STREAM: the
+// indices are read once per step (evict-first), else through the read-only cache.
 template <int SW, bool HAS_W, bool LD_STREAM, class VJ>
 __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col16, const float *__restrict__ w,
                                                int e0, int e1, float vi, int li, VJ vj) {
     float acc = 0.0f;
     const int ea = min(e1, (e0 + 7) & ~7);                 // first 16-byte aligned edge
     const int eb = ea + ((e1 - ea) & ~7);                   // end of the aligned body
-    for (int e = e0 + li; e < ea; e += SW) acc += gj_edge(vi, vj(col16[e]), HAS_W ? __ldg(w + e) : 1.0f);
-    for (int e = ea + 8 * li; e < eb; e += 8 * SW) {
-        const uint4 q = LD_STREAM ? __ldcs(reinterpret_cast<const uint4 *>(col16 + e))
-                                  : __ldg(reinterpret_cast<const uint4 *>(col16 + e));
-        float4 wa = make_float4(1.0f, 1.0f, 1.0f, 1.0f), wb = wa;
-        if (HAS_W) {
-            wa = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e)) : __ldg(reinterpret_cast<const float4 *>(w + e));
-            wb = LD_STREAM ? __ldcs(reinterpret_cast<const float4 *>(w + e + 4))
-                           : __ldg(reinterpret_cast<const float4 *>(w + e + 4));
-        }
-        const float v0 = vj(q.x & 0xFFFFu), v1 = vj(q.x >> 16), v2 = vj(q.y & 0xFFFFu), v3 = vj(q.y >> 16);
-        const float v4 = vj(q.z & 0xFFFFu), v5 = vj(q.z >> 16), v6 = vj(q.w & 0xFFFFu), v7 = vj(q.w >> 16);
-        acc += ((gj_edge(vi, v0, wa.x) + gj_edge(vi, v1, wa.y)) + (gj_edge(vi, v2, wa.z) + gj_edge(vi, v3, wa.w))) +
-               ((gj_edge(vi, v4, wb.x) + gj_edge(vi, v5, wb.y)) + (gj_edge(vi, v6, wb.z) + gj_edge(vi, v7, wb.w)));
+    int e = ea + 8 * li;
+    if (SW >= 8) {
+        const int eh = e0 + li, et = eb + li;
+        const bool hh = eh < ea, ht = et < e1;
+        const uint32_t jh = hh ? csr_ld16<LD_STREAM>(col16, eh) : 0u;
+        const uint32_t jt = ht ? csr_ld16<LD_STREAM>(col16, et) : 0u;
+        const float wh = (HAS_W && hh) ? __ldg(w + eh) : 1.0f, wt = (HAS_W && ht) ? __ldg(w + et) : 1.0f;
+        const bool g0 = e < eb, g1 = e + 8 * SW < eb;
+        uint4 q0 = make_uint4(0u, 0u, 0u, 0u), q1 = q0;
+        float4 a0 = make_float4(1.0f, 1.0f, 1.0f, 1.0f), b0 = a0, a1 = a0, b1 = a0;
+        if (g0) csr_load16<HAS_W, LD_STREAM>(col16, w, e, q0, a0, b0);
+        if (g1) csr_load16<HAS_W, LD_STREAM>(col16, w, e + 8 * SW, q1, a1, b1);
+        if (hh) acc += gj_edge(vi, vj(jh), wh);
+        if (ht) acc += gj_edge(vi, vj(jt), wt);
+        if (g0) acc += csr_group16<HAS_W>(q0, a0, b0, vi, vj);
+        if (g1) acc += csr_group16<HAS_W>(q1, a1, b1, vi, vj);
+        e += 16 * SW;
+    } else {
+        for (int eh = e0 + li; eh < ea; eh += SW) acc += gj_edge(vi, vj(csr_ld16<LD_STREAM>(col16, eh)), HAS_W ? __ldg(w + eh) : 1.0f);
     }
-    for (int e = eb + li; e < e1; e += SW) acc += gj_edge(vi, vj(col16[e]), HAS_W ? __ldg(w + e) : 1.0f);
+    for (; e + 8 * SW < eb; e += 16 * SW) {                 // further rounds: two groups in flight
+        uint4 q0, q1;
+        float4 a0, b0, a1, b1;
+        csr_load16<HAS_W, LD_STREAM>(col16, w, e, q0, a0, b0);
+        csr_load16<HAS_W, LD_STREAM>(col16, w, e + 8 * SW, q1, a1, b1);
+        acc += csr_group16<HAS_W>(q0, a0, b0, vi, vj) + csr_group16<HAS_W>(q1, a1, b1, vi, vj);
+    }
+    if (e < eb) {
+        uint4 q;
+        float4 a, b;
+        csr_load16<HAS_W, LD_STREAM>(col16, w, e, q, a, b);
+        acc += csr_group16<HAS_W>(q, a, b, vi, vj);
+    }
+    if (SW < 8)
+        for (int et = eb + li; et < e1; et += SW) acc += gj_edge(vi, vj(csr_ld16<LD_STREAM>(col16, et)), HAS_W ? __ldg(w + et) : 1.0f);
     return acc;
 }
 

@@ -14,7 +14,6 @@ namespace ion {
 constexpr int TJ = 8192;
 constexpr int CSR_CHUNK = 32768;   // floats of V_dend per shared-memory chunk (128 KB)
 static_assert(CSR_CHUNK <= 65536, "16-bit chunk-relative columns need chunks of at most 2^16 cells");
-constexpr int CSR_SCHUNK = 16384;  // cells per chunk of the streamed (chunk-major) CSR kernel (64 KB)
 constexpr int PAD_J = 256;
 constexpr float PAD_VOLT = 1.0e7f;
 
@@ -104,6 +103,10 @@ struct HalfArgs {
     float *usum;           // [grid] sum of u over each CTA's own rows
     int32_t chunk;         // tile columns per column-partial round (a multiple of 128; set by the launcher)
 };
+struct MatrixArgs {
+    StepCommon c;
+    const float *W;       // n rows x n_pad columns, row-major, zero beyond column n
+};
 struct CellArgs {
     StepCommon c;
     const float *ic;      // NULL: no gap current
@@ -115,6 +118,11 @@ cudaError_t launch_csr_step(const CsrArgs &a, int lanes_per_row, int rows_per_ct
 cudaError_t prepare_csr_step();
 cudaError_t launch_csr_chunk_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *mid,
                                   int n_chunks, bool prepare, cudaStream_t st);
+cudaError_t prepare_matrix_step(int n_pad);
+cudaError_t launch_matrix_step(const MatrixArgs &a, cudaStream_t st);
+int sgj_partials(int n);   // CTAs of the SGJ partial-sum launch (the update reads that many)
+cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st);
+cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st);
 cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st);
 cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
                                     int32_t *mid, cudaStream_t st);

@@ -21,13 +21,8 @@ struct ion_sim {
     float *d_w = nullptr;
     bool own_csr = false;
     uint16_t *d_col16 = nullptr;    // low 16 bits of every column (compact CSR layout)
-    // chunk-major CSR of the streamed kernel (csr_staged == 2): row bounds per chunk,
-    // chunk-relative 16-bit columns, weights in the same order; ring shape
-    int32_t *d_crp = nullptr;
-    uint16_t *d_ccol = nullptr;
-    float *d_cw = nullptr;
-    int stream_nc = 0, stream_rows = 0, stream_se = 0, stream_ns = 0;
-    size_t stream_smem = 0;
+    float *d_sgj = nullptr;         // SGJ dense: per-CTA partial sums of V_dend - m
+    float *d_W = nullptr;           // dense matrix: n rows x n_pad columns (zero padded)
     // state and bookkeeping
     float *d_state = nullptr;       // 20 * stride floats
     float *d_ic = nullptr;          // gap currents (split mode)
@@ -87,8 +82,7 @@ struct ion_sim {
 
 // shared helpers (ion_api.cu)
 void ion_csr_fill(const ion_sim *s, ion::CsrArgs &a, bool staged);
-ion_status ion_setup_csr_stream(ion_sim *s);                                   // ion_csr_stream.cu
-cudaError_t launch_csr_stream(const ion_sim *s, const ion::StepCommon &c, cudaStream_t st);
+ion_status ion_prepare_csr_chunk(ion_sim *s);
 ion_status ion_fail(ion_sim *s, ion_status code, const char *fmt, ...);
 ion::ModelF ion_model_to_f32(const ion_model &m, double dt);
 ion::StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp);

@@ -150,6 +150,11 @@ def config(name: str, k: int | None = None, n: int | None = None) -> dict:
         sub = random_subset(n, 0.2, 3)
         return dict(name=f"{name}_n{n}", n=n, kind="ngj", jitter=vdend_jitter(n, 3),
                     pulses=pulses(sub, 5.0, 15.0, 6.0), n_steps=400)
+    if name == "c2_matrix":   # 8192 cells, every pair weighted: W_ij = g_c(N) * U(0, 2), seed 1
+        n = 8192
+        g = junction_weight(0.04, n)
+        W = (g * uniform(stream_seed(1, "matrix_w"), n * n, 0.0, 2.0)).astype(np.float32).reshape(n, n)
+        return dict(name=name, n=n, kind="matrix", W=W, jitter=vdend_jitter(n, 1), pulses=None, n_steps=4000)
     if name == "c1_spiking":   # c1 with every cell pulsed at 100-110, 400-410 and 700-710 ms
         n = 64
         cells = np.arange(n)

@@ -24,10 +24,11 @@ GATES = ("r", "s", "q", "k", "l", "m_s", "h_s", "n_s", "x_s", "m_a", "h_a", "x_a
 
 OK, ERR_INVALID_ARG, ERR_BAD_CSR, ERR_OOM, ERR_CUDA, ERR_NONFINITE, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 STATUS_NAMES = ("OK", "INVALID_ARG", "BAD_CSR", "OOM", "CUDA", "NONFINITE", "TIMEOUT", "UNSUPPORTED")
-DENSE_UNIFORM, CSR, NO_GJ = 0, 1, 2
+DENSE_UNIFORM, CSR, NO_GJ, DENSE_MATRIX = 0, 1, 2, 3
 HOST, DEVICE = 0, 1
 FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SPLIT, FLAG_HALF_WORK = 1, 2, 4, 8, 16, 32, 64
 FLAG_CSR_AS_GIVEN = 128
+FLAG_SGJ = 256           # SGJ use case: linear junctions w (V_i - V_j)
 INPUT_NONE, INPUT_PULSES, INPUT_DENSE = 0, 1, 2
 MLP_IN, MLP_HID, MLP_OUT = 2, 64, 24
 
@@ -216,6 +217,13 @@ def _conn_struct(kind, g=0.0, row_ptr=None, col=None, w=None):
         c.col_idx = _ptr(col, ctypes.c_int32)
         c.weight = _ptr(w, ctypes.c_float)
         c.nnz = int(len(col) if not dev else col.numel())
+        c.mem = DEVICE if dev else HOST
+    elif kind == DENSE_MATRIX:   # w: n x n row-major weights (host array or device tensor)
+        dev = _is_device(w)
+        if not dev:
+            w = np.ascontiguousarray(w, np.float32)
+        keep.append(w)
+        c.weight = _ptr(w, ctypes.c_float)
         c.mem = DEVICE if dev else HOST
     return c, keep
 

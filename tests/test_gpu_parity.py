@@ -396,11 +396,10 @@ def test_csr_shared_memory_staging(torch_cuda, O, n, k, staging):
 @pytest.mark.parametrize("n,k,staging", [(3001, 48, 1), (3001, 12, 1), (3001, 24, 2), (70000, 40, 1), (70000, 300, 2)])
 @pytest.mark.parametrize("weights", ["uniform", "random", "as_given"])
 def test_csr_compact_layouts(torch_cuda, O, n, k, staging, weights):
-    """The compact CSR layouts (16-bit columns; one scalar for bitwise-equal weights; with
-    staging, the chunk-major layout streamed by bulk copies) and the layout as given all
-    reproduce the oracle's step; the handle reports what it streams per edge: 16-bit
-    columns when V_dend is staged in chunks, or n <= 65 536 with rows of at least 32
-    edges on average."""
+    """The compact CSR layouts (16-bit columns; one scalar for bitwise-equal weights) and
+    the layout as given all reproduce the oracle's step; the handle reports what it
+    streams per edge: 16-bit columns when V_dend is staged in chunks, or n <= 65 536 with
+    rows of at least 32 edges on average."""
     rp, col = inputs.random_symmetric_csr(n, k, 29)
     g = inputs.junction_weight(0.04, k)
     if weights == "random":
@@ -411,12 +410,7 @@ def test_csr_compact_layouts(torch_cuda, O, n, k, staging, weights):
     tune = dict(csr_staging=staging)
     with ion.Simulation(n, ion.CSR, row_ptr=rp, col=col, w=w, flags=flags, tune=tune) as sim:
         lay = ion.ion_csr_layout(sim.h)
-    if staging == 1:
-        assert lay["staged"] == 0
-    elif weights == "as_given":
-        assert lay["staged"] == 1             # V_dend chunks, row-major CSR
-    else:
-        assert lay["staged"] == 2             # V_dend chunks, chunk-major CSR streamed by bulk copies
+    assert lay["staged"] == (1 if staging == 2 else 0)
     if weights == "as_given":
         assert lay == dict(index_bytes=4, weight_bytes=4, staged=lay["staged"])
     else:
@@ -425,3 +419,101 @@ def test_csr_compact_layouts(torch_cuda, O, n, k, staging, weights):
         assert lay["weight_bytes"] == (0 if weights == "uniform" else 4)
     err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=3, flags=flags, tune=tune)
     assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+# ------------------------------------------------------------------ SGJ use case (linear junctions)
+
+def _sgj_one_step(O, n, kind, g=0.0, rp=None, col=None, w=None):
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 41))
+    S0 = initial_state(O, cfg)
+    k_or = O.DENSE_SGJ if kind == O.DENSE else O.CSR_SGJ
+    wd = None if w is None else w.astype(np.float64)
+    Sw, _ = O.run(S0.astype(np.float64), 30, kind=k_or, g=g, row_ptr=rp, col=col, w=wd, threads=_threads(O))
+    Sw32 = Sw.astype(np.float32)
+    iapp = inputs.uniform(inputs.stream_seed(n, "iapp_sgj"), n, 0.0, 4.0).astype(np.float32)
+    ref, _ = O.run(Sw32.astype(np.float64), 1, kind=k_or, g=g, row_ptr=rp, col=col, w=wd, t0=0,
+                   iapp_dense=iapp[None, :], threads=_threads(O))
+    ikind = ion.DENSE_UNIFORM if kind == O.DENSE else ion.CSR
+    with ion.Simulation(n, ikind, g=g, row_ptr=rp, col=col, w=w, init_state=Sw32,
+                        flags=ion.FLAG_KAHAN | ion.FLAG_SGJ) as sim:
+        sim.step(1, dense=iapp[None, :])
+        got = sim.state()
+    scale = g * sum_abs_dv(Sw32[0]) if kind == O.DENSE else csr_abs_scale(rp, col, w, Sw32[0])
+    return step_rel_err(got, ref, scale)
+
+
+@pytest.mark.parametrize("n", [1, 300, 8192])
+def test_sgj_dense_one_step(torch_cuda, O, n):
+    err = _sgj_one_step(O, n, O.DENSE, g=float(np.float32(inputs.junction_weight(0.04, n))))
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+@pytest.mark.parametrize("n,k,weights", [(65536, 100, "uniform"), (1000, 7, "random")])
+def test_sgj_csr_one_step(torch_cuda, O, n, k, weights):
+    rp, col = inputs.random_symmetric_csr(n, k, 17)
+    g = inputs.junction_weight(0.04, k)
+    w = np.full(len(col), g, np.float32)
+    if weights == "random":
+        w = (w * inputs.uniform(inputs.stream_seed(n, "sgj_w"), len(col), 0.5, 1.5)).astype(np.float32)
+    err = _sgj_one_step(O, n, O.CSR, rp=rp, col=col, w=w)
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+def test_sgj_c1_trajectory_100ms(torch_cuda, O):
+    """The 64-cell network with linear junctions: within 0.1 mV of the oracle for 100 ms."""
+    cfg = inputs.config("c1")
+    n = cfg["n"]
+    S0 = initial_state(O, cfg)
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=cfg["g"], init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_SGJ) as sim:
+        sim.set_input(cfg["pulses"])
+        sim.step(2000)
+        got = sim.state()
+    ref, _ = O.run(S0.astype(np.float64), 2000, kind=O.DENSE_SGJ, g=cfg["g"], pulses=cfg["pulses"],
+                   threads=_threads(O))
+    assert np.abs(got[:3] - ref[:3]).max() <= TRAJ_MV
+
+
+# ------------------------------------------------------------------ dense N x N weight matrix
+
+def _matrix(n, seed):
+    g = inputs.junction_weight(0.04, n)
+    return (g * inputs.uniform(inputs.stream_seed(seed, "matrix_w"), n * n, 0.0, 2.0)).astype(np.float32).reshape(n, n)
+
+
+@pytest.mark.parametrize("n", [1, 300, 3001, 9000])
+def test_matrix_one_step(torch_cuda, O, n):
+    """One step with an asymmetric random weight matrix (one or two V_dend tiles, a ragged
+    last CTA) from an identical state, against the FP64 oracle; the I_c floor is the
+    scale of its terms, sum_j |W_ij| |dV_ij|."""
+    W = _matrix(n, 50)
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 51))
+    S0 = initial_state(O, cfg)
+    Wd = W.astype(np.float64)
+    Sw, _ = O.run(S0.astype(np.float64), 5, kind=O.MATRIX, w=Wd, threads=_threads(O))
+    Sw32 = Sw.astype(np.float32)
+    ref, _ = O.run(Sw32.astype(np.float64), 1, kind=O.MATRIX, w=Wd, threads=_threads(O))
+    with ion.Simulation(n, ion.DENSE_MATRIX, w=W, init_state=Sw32) as sim:
+        sim.step(1)
+        got = sim.state()
+    vd = Sw32[0].astype(np.float64)
+    scale = np.array([np.abs(Wd[i]) @ np.abs(vd[i] - vd) for i in range(n)])
+    err = step_rel_err(got, ref, scale)
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+def test_matrix_from_device_tensor_and_uniform_matches_dense(torch_cuda, O):
+    """A device-resident matrix is copied like a host one, and a uniform matrix gives the
+    uniform dense network's trajectory (different summation order: close, not equal)."""
+    torch = torch_cuda
+    n = 1000
+    g = float(np.float32(inputs.junction_weight(0.04, n)))
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 52))
+    S0 = initial_state(O, cfg)
+    Wt = torch.full((n, n), g, dtype=torch.float32, device="cuda")
+    with ion.Simulation(n, ion.DENSE_MATRIX, w=Wt, init_state=S0) as sim:
+        sim.step(400)
+        a = sim.state()
+    with ion.Simulation(n, ion.DENSE_UNIFORM, g=g, init_state=S0) as sim:
+        sim.step(400)
+        b = sim.state()
+    assert np.abs(a[:3] - b[:3]).max() <= 1e-3
