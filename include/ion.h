@@ -248,6 +248,17 @@ ion_status ion_state_device_ptr(ion_sim *sim, int32_t field, float **out);
 ion_status ion_set_trace(ion_sim *sim, int32_t stride, int32_t capacity);
 ion_status ion_read_trace(ion_sim *sim, float *out, int64_t max_samples, int64_t *n_written);
 
+/* Asynchronous form of ion_read_trace (Sec. 2.4.3: the transfer of step t overlaps the
+ * computation of step t + 1): queues, on the handle's own copy stream and after the steps
+ * already enqueued, the copy of the samples recorded since the last read (oldest first,
+ * out[s * n_cells + i]) and returns at once with *n_queued.  `out` must stay valid until
+ * ion_trace_wait (or ion_destroy) returns; pinned host memory lets the copy overlap the
+ * steps that follow.  Later steps that would overwrite a ring slot the copy still reads
+ * wait for it on the device.  Not for batches (ION_ERR_UNSUPPORTED). */
+ion_status ion_read_trace_async(ion_sim *sim, float *out, int64_t max_samples, int64_t *n_queued);
+/* Block until the last queued trace copy has landed in host memory. */
+ion_status ion_trace_wait(ion_sim *sim);
+
 /* Time candidate launch shapes on this handle's own network(s), `steps` time steps each,
  * and keep the fastest (the state and step count are restored afterwards).  Single
  * dense networks: (R, W, GJ) near the cost model's optimum; single CSR networks: lanes

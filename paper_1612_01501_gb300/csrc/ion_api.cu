@@ -465,6 +465,11 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
                                   conn->mem == ION_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st);
         if (e == cudaSuccess) e = prepare_matrix_step(s->n_pad);
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: matrix copy: %s", cudaGetErrorString(e)));
+        s->dense_R = matrix_default_R(s->n, sms);
+        const ion_tune *tu = (const ion_tune *)params->tune;
+        if (tu && tu->dense_rows_per_warp > 0) s->dense_R = tu->dense_rows_per_warp;
+        if (s->dense_R != 1 && s->dense_R != 2 && s->dense_R != 4)
+            return fail(ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: matrix rows per warp %d unsupported", s->dense_R));
     } else if (s->kind == ION_CSR) {
         s->g = conn->g_c;
         s->nnz = conn->nnz;
@@ -540,6 +545,12 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
 extern "C" void ion_destroy(ion_sim *s) {
     if (!s) return;
     cudaStreamSynchronize(s->st);
+    if (s->copy_st) {
+        cudaStreamSynchronize(s->copy_st);
+        cudaStreamDestroy(s->copy_st);
+        cudaEventDestroy(s->ev_ready);
+        cudaEventDestroy(s->ev_copied);
+    }
     ion_sim_free_device(s);
     if (s->own_stream) cudaStreamDestroy(s->own_stream);
     delete s;
@@ -652,7 +663,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
         MatrixArgs a{};
         a.c = c;
         a.W = s->d_W;
-        e = launch_matrix_step(a, s->st);
+        e = launch_matrix_step(a, s->dense_R, s->st);
         s->launches++;
         return e;
     }
@@ -789,6 +800,12 @@ extern "C" ion_status ion_step(ion_sim *s, int64_t n_steps, const ion_input *inp
         ion_status st = s->prepare_hook(s);
         if (st != ION_OK) return st;
     }
+    // a pending asynchronous trace copy still reads ring slots: steps that would write the
+    // sample taking the first of them wait for the copy
+    if (s->copy_pending && s->trace_stride > 0 && (s->t + n_steps) / s->trace_stride > s->copy_guard_sample) {
+        ION_CK(s, cudaStreamWaitEvent(s->st, s->ev_copied, 0));
+        s->copy_guard_sample = INT64_MAX;   // ordered after the copy; the host still waits in ion_trace_wait
+    }
     if (s->run_override && iapp == nullptr) {
         ion_status st = s->run_override(s, n_steps, iapp);
         if (st != ION_OK) return st;
@@ -919,6 +936,8 @@ extern "C" ion_status ion_set_step_count(ion_sim *s, int64_t t) {
 extern "C" ion_status ion_set_trace(ion_sim *s, int32_t stride, int32_t capacity) {
     if (!s || stride < 0 || capacity < 0) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_set_trace: bad arguments");
     ION_CK(s, cudaStreamSynchronize(s->st));
+    if (s->copy_st) ION_CK(s, cudaStreamSynchronize(s->copy_st));
+    s->copy_pending = false;
     cudaFree(s->d_trace);
     s->d_trace = nullptr;
     s->trace_stride = 0;
@@ -964,6 +983,54 @@ extern "C" ion_status ion_read_trace(ion_sim *s, float *out, int64_t max_samples
     s->trace_read = first + take;
     *n_written = take;
     return st;
+}
+
+// Asynchronous drain of the V_axon ring: the copy runs on the handle's copy stream after
+// the steps already enqueued, so later steps overlap it (the paper's GPU design overlaps
+// the transfer of step t with the computation of step t + 1, Sec. 2.4.3).  Steps that
+// would overwrite a slot the pending copy still reads wait for it first.
+extern "C" ion_status ion_read_trace_async(ion_sim *s, float *out, int64_t max_samples, int64_t *n_queued) {
+    if (!s || !n_queued) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_trace_async: NULL argument");
+    *n_queued = 0;
+    if (!s->d_trace) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_trace_async: tracing is off");
+    if (s->d_map) return ion_fail(s, ION_ERR_UNSUPPORTED, "ion_read_trace_async: not for batches (use ion_read_trace)");
+    if (max_samples < 0) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_trace_async: negative max_samples");
+    const int64_t produced = s->t / s->trace_stride;
+    int64_t first = s->trace_read;
+    if (produced - first > s->trace_cap) first = produced - s->trace_cap;   // overwritten samples are lost
+    const int64_t take = std::min(produced - first, max_samples);
+    if (take > 0 && !out) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_read_trace_async: NULL out");
+    if (!s->copy_st) {
+        ION_CK(s, cudaStreamCreateWithFlags(&s->copy_st, cudaStreamNonBlocking));
+        ION_CK(s, cudaEventCreateWithFlags(&s->ev_ready, cudaEventDisableTiming));
+        ION_CK(s, cudaEventCreateWithFlags(&s->ev_copied, cudaEventDisableTiming));
+    }
+    if (take > 0) {
+        ION_CK(s, cudaEventRecord(s->ev_ready, s->st));
+        ION_CK(s, cudaStreamWaitEvent(s->copy_st, s->ev_ready, 0));
+        const int64_t slot0 = first % s->trace_cap;
+        const int64_t k1 = std::min(take, s->trace_cap - slot0);    // up to the ring's end, then from slot 0
+        ION_CK(s, cudaMemcpyAsync(out, s->d_trace + slot0 * s->n, (size_t)(k1 * s->n) * sizeof(float),
+                                  cudaMemcpyDeviceToHost, s->copy_st));
+        if (take > k1)
+            ION_CK(s, cudaMemcpyAsync(out + k1 * s->n, s->d_trace, (size_t)((take - k1) * s->n) * sizeof(float),
+                                      cudaMemcpyDeviceToHost, s->copy_st));
+        ION_CK(s, cudaEventRecord(s->ev_copied, s->copy_st));
+        s->copy_pending = true;
+        s->copy_guard_sample = first + s->trace_cap;
+    }
+    s->trace_read = first + take;
+    *n_queued = take;
+    return ION_OK;
+}
+
+extern "C" ion_status ion_trace_wait(ion_sim *s) {
+    if (!s) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_trace_wait: NULL handle");
+    if (s->copy_pending) {
+        ION_CK(s, cudaEventSynchronize(s->ev_copied));
+        s->copy_pending = false;
+    }
+    return ION_OK;
 }
 
 // ---- single-launch primitives ---------------------------------------------------------------

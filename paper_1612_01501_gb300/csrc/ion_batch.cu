@@ -681,6 +681,23 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         bt.dense_rows_per_warp = bs.R;
         bt.dense_warps = bs.W;
         bt.dense_col_splits = bs.GJ;
+    } else if (s->kind == ION_DENSE_MATRIX) {
+        int bR = s->dense_R;
+        for (int R : {1, 2, 4}) {
+            s->dense_R = R;
+            float ms = 0;
+            st = time_steps(s, steps, &ms);
+            restore();
+            if (st != ION_OK) break;
+            if (ms < best) {
+                best = ms;
+                bR = R;
+            }
+        }
+        s->dense_R = bR;
+        bt.dense_rows_per_warp = bR;
+        bt.dense_warps = 8;
+        bt.dense_col_splits = 1;
     } else if (s->kind == ION_CSR) {
         const int SWs[] = {1, 2, 4, 8, 16, 32};
         const int rows[] = {32, 64, 128, 256};

@@ -119,7 +119,8 @@ cudaError_t prepare_csr_step();
 cudaError_t launch_csr_chunk_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *mid,
                                   int n_chunks, bool prepare, cudaStream_t st);
 cudaError_t prepare_matrix_step(int n_pad);
-cudaError_t launch_matrix_step(const MatrixArgs &a, cudaStream_t st);
+cudaError_t launch_matrix_step(const MatrixArgs &a, int R, cudaStream_t st);   // R: rows per warp, 1, 2 or 4
+int matrix_default_R(int n, int sms);
 int sgj_partials(int n);   // CTAs of the SGJ partial-sum launch (the update reads that many)
 cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st);
 cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st);

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
-#pragma unroll 2
+#pragma unroll 4
             for (int mm = 0; mm < BLK; ++mm) {
                 const int mq = m0 + mm * 32;
                 if (mq < n4) {
@@ -132,20 +132,37 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
     finish_cell(c, t, vnext, i, o);
 }
 
-constexpr int MATRIX_R = 4;   // rows per warp (32 rows per CTA)
-
 size_t matrix_smem_bytes(int n_pad) { return (size_t)(n_pad > TJ ? 2 * TJ : n_pad) * sizeof(float); }
 
 cudaError_t prepare_matrix_step(int n_pad) {
-    return cudaFuncSetAttribute(matrix_step_kernel<MATRIX_R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)matrix_smem_bytes(n_pad));
+    const int smem = (int)matrix_smem_bytes(n_pad);
+    cudaError_t e = cudaFuncSetAttribute(matrix_step_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(matrix_step_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(matrix_step_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    return e;
 }
 
-cudaError_t launch_matrix_step(const MatrixArgs &a, cudaStream_t st) {
-    const int rows = 8 * MATRIX_R;
-    const int grid = (a.c.n + rows - 1) / rows;
-    matrix_step_kernel<MATRIX_R><<<grid, 256, matrix_smem_bytes(a.c.n_pad), st>>>(a);
+// rows per warp: the largest of 4, 2, 1 that still gives about six CTAs per SM (the
+// weight stream needs many warps in flight; at 8192 cells R = 1 measured fastest), else 1
+int matrix_default_R(int n, int sms) {
+    for (int R : {4, 2})
+        if ((n + 8 * R - 1) / (8 * R) >= 6 * sms) return R;
+    return 1;
+}
+
+template <int R>
+static cudaError_t matrix_launch_R(const MatrixArgs &a, cudaStream_t st) {
+    const int grid = (a.c.n + 8 * R - 1) / (8 * R);
+    matrix_step_kernel<R><<<grid, 256, matrix_smem_bytes(a.c.n_pad), st>>>(a);
     return cudaGetLastError();
+}
+cudaError_t launch_matrix_step(const MatrixArgs &a, int R, cudaStream_t st) {
+    switch (R) {
+        case 1: return matrix_launch_R<1>(a, st);
+        case 2: return matrix_launch_R<2>(a, st);
+        case 4: return matrix_launch_R<4>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace ion

@@ -42,6 +42,12 @@ struct ion_sim {
     float *d_trace = nullptr;
     int32_t trace_stride = 0, trace_cap = 0;
     int64_t trace_read = 0;
+    // asynchronous trace drain: copy stream, events, and the first sample index whose slot
+    // a pending copy still reads (steps producing it wait for the copy)
+    cudaStream_t copy_st = nullptr;
+    cudaEvent_t ev_ready = nullptr, ev_copied = nullptr;
+    bool copy_pending = false;
+    int64_t copy_guard_sample = 0;
     // model and launch configuration
     ion_model model{};
     ion::ModelF P{};

@@ -107,6 +107,8 @@ _SIGS = {
     "ion_state_device_ptr": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]),
     "ion_set_trace": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32]),
     "ion_read_trace": (ctypes.c_int, [ctypes.c_void_p, c_f32p, ctypes.c_int64, c_i64p]),
+    "ion_read_trace_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, c_i64p]),
+    "ion_trace_wait": (ctypes.c_int, [ctypes.c_void_p]),
     "ion_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "ion_csr_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
@@ -359,6 +361,20 @@ def ion_read_trace(h, n: int, max_samples: int) -> np.ndarray:
     got = ctypes.c_int64()
     _check(lib().ion_read_trace(h, _ptr(out, ctypes.c_float), int(max_samples), ctypes.byref(got)), h)
     return out[:got.value]
+
+
+def ion_read_trace_async(h, out, max_samples: int) -> int:
+    """Queue the copy of the recorded samples into `out` (a pinned host tensor or a numpy
+    array of at least max_samples x n floats, kept alive by the caller until
+    ion_trace_wait); returns the number of samples queued."""
+    got = ctypes.c_int64()
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _check(lib().ion_read_trace_async(h, ctypes.c_void_p(ptr), int(max_samples), ctypes.byref(got)), h)
+    return got.value
+
+
+def ion_trace_wait(h):
+    _check(lib().ion_trace_wait(h), h)
 
 
 def ion_autotune(h, steps: int = 20) -> dict:

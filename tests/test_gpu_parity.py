@@ -480,8 +480,8 @@ def _matrix(n, seed):
     return (g * inputs.uniform(inputs.stream_seed(seed, "matrix_w"), n * n, 0.0, 2.0)).astype(np.float32).reshape(n, n)
 
 
-@pytest.mark.parametrize("n", [1, 300, 3001, 9000])
-def test_matrix_one_step(torch_cuda, O, n):
+@pytest.mark.parametrize("n,R", [(1, 0), (300, 0), (3001, 1), (3001, 2), (3001, 4), (9000, 0)])
+def test_matrix_one_step(torch_cuda, O, n, R):
     """One step with an asymmetric random weight matrix (one or two V_dend tiles, a ragged
     last CTA) from an identical state, against the FP64 oracle; the I_c floor is the
     scale of its terms, sum_j |W_ij| |dV_ij|."""
@@ -492,7 +492,8 @@ def test_matrix_one_step(torch_cuda, O, n):
     Sw, _ = O.run(S0.astype(np.float64), 5, kind=O.MATRIX, w=Wd, threads=_threads(O))
     Sw32 = Sw.astype(np.float32)
     ref, _ = O.run(Sw32.astype(np.float64), 1, kind=O.MATRIX, w=Wd, threads=_threads(O))
-    with ion.Simulation(n, ion.DENSE_MATRIX, w=W, init_state=Sw32) as sim:
+    tune = dict(dense_rows_per_warp=R) if R else None    # 0: the library's choice
+    with ion.Simulation(n, ion.DENSE_MATRIX, w=W, init_state=Sw32, tune=tune) as sim:
         sim.step(1)
         got = sim.state()
     vd = Sw32[0].astype(np.float64)
@@ -517,3 +518,38 @@ def test_matrix_from_device_tensor_and_uniform_matches_dense(torch_cuda, O):
         sim.step(400)
         b = sim.state()
     assert np.abs(a[:3] - b[:3]).max() <= 1e-3
+
+
+# ------------------------------------------------------------------ asynchronous trace drain
+
+def test_trace_async_drain_matches_sync_read(torch_cuda, O):
+    """V_axon samples drained asynchronously (copy stream, pinned buffer, steps enqueued
+    behind the copy) equal the synchronous reads of an identical run, through a ring of
+    600 samples drained every 500 steps (it wraps, and later steps must wait for the copy
+    still reading the slots they overwrite)."""
+    torch = torch_cuda
+    cfg = inputs.config("c1_spiking")
+    n, rounds, per = cfg["n"], 6, 500
+    S0 = initial_state(O, cfg)
+    outs = []
+    for mode in ("async", "sync"):
+        with ion.Simulation(n, ion.DENSE_UNIFORM, g=cfg["g"], init_state=S0) as sim:
+            sim.set_input(cfg["pulses"])
+            ion.ion_set_trace(sim.h, 1, 600)
+            if mode == "async":
+                buf = torch.empty((rounds * per, n), dtype=torch.float32).pin_memory()
+                got = 0
+                for r in range(rounds):
+                    sim.step(per)
+                    got += ion.ion_read_trace_async(sim.h, buf[got:], rounds * per - got)
+                ion.ion_trace_wait(sim.h)
+                assert got == rounds * per
+                outs.append(buf.numpy().copy())
+            else:
+                parts = []
+                for r in range(rounds):
+                    sim.step(per)
+                    parts.append(ion.ion_read_trace(sim.h, n, per))
+                outs.append(np.concatenate(parts))
+    np.testing.assert_array_equal(outs[0], outs[1])
+    assert len(O.spike_steps(outs[0][:, 0])) >= 2       # the drained trace holds real spikes
