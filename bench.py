@@ -46,6 +46,14 @@ WORKLOADS = {
     "c2_matrix": dict(name="c2_matrix_dense_8192_NxN_weights_100ms", cfg="c2_matrix", steps=2000),
 }
 K3_SWEEP = (1 << 16, 1 << 18, 1 << 20, 1 << 22)
+# DRAM bytes (read + write) per launch of the line's dominant kernel, from one ncu capture
+# of that kernel in its current form (the summaries under profiles/ give the commands);
+# None where no capture matches the line's kernel and shape
+TRAFFIC = {
+    ("c2", "dense_step_kernel"): (525.0e3, "profiles/dense_step_kernel_c2_8192.md"),
+    ("c3_k1000", "csr_chunk_step_kernel"): (139.5e6, "profiles/csr_chunk_step_kernel_c3_k1000_compact.md"),
+    ("k3", "cell_step_kernel"): (517.0e6, "profiles/cell_step_kernel_k3_4194304.md"),
+}
 
 
 def parse():
@@ -569,6 +577,10 @@ def main():
             "gpu_launches": int(launches),
             "clocks": ck,
         }
+        tr = TRAFFIC.get((key, roof.get("kernel")))
+        if tr is not None and (key != "c3_k1000" or best == "graph"):
+            roof["traffic"] = tr[0]
+            roof["traffic_source"] = tr[1]
         # the paper's real-time criterion: one time step (50 us of biological time) computed
         # in at most 50 us of wall time
         line["real_time"] = {"us_per_timestep": roof["us_per_timestep"], "limit_us": 50.0,
