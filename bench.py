@@ -255,8 +255,9 @@ def load_workload(key):
     return inputs.config(w["cfg"], k=w.get("k"), n=w.get("n"))
 
 
-def cpu_baseline(key, sample_steps):
-    """FP64 oracle on all host cores: `sample_steps` time steps of the workload."""
+def cpu_baseline(key, sample_steps, single_thread_steps=0):
+    """FP64 oracle on all host cores: `sample_steps` time steps of the workload (and, if
+    single_thread_steps > 0, that many more on one core, reported beside it)."""
     import oracle as O
     cfg = load_workload(key)
     threads = O.max_threads()
@@ -279,9 +280,17 @@ def cpu_baseline(key, sample_steps):
         O.run(S, sample_steps, **kw)
     dt = time.perf_counter() - t0
     v = cfg["n"] * sample_steps / dt
-    return {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
-            "sample": f"{sample_steps} time steps of {WORKLOADS[key]['name']} (FP64, OpenMP over cells)",
-            "seconds": dt}
+    out = {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
+           "sample": f"{sample_steps} time steps of {WORKLOADS[key]['name']} (FP64, OpenMP over cells)",
+           "seconds": dt}
+    if single_thread_steps > 0:
+        t0 = time.perf_counter()
+        for S, kw in runs:
+            O.run(S, single_thread_steps, **dict(kw, threads=1))
+        d1 = time.perf_counter() - t0
+        out["single_core"] = {"value": cfg["n"] * single_thread_steps / d1, "unit": METRIC, "cores": 1,
+                              "sample": f"{single_thread_steps} time steps, one thread"}
+    return out
 
 
 def reference_sample_steps(key):
@@ -606,8 +615,9 @@ def main():
         if rank == 0:
             line["e2e"] = {"value": e2e_value, "unit": METRIC,
                            "h2d_bytes_per_step": int(S0.nbytes), "d2h_bytes_per_step": int(S0.nbytes)}
-            cpu = cpu_baseline(key, reference_sample_steps(key) if key != "c2" else 3)
-            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            ks = reference_sample_steps(key) if key != "c2" else 3
+            cpu = cpu_baseline(key, ks, single_thread_steps=max(1, ks // 4))
+            line["cpu_baseline"] = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample", "single_core")}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()

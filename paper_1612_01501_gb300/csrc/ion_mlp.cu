@@ -456,8 +456,10 @@ __global__ void __launch_bounds__(128) mlp_eval_kernel(const MlpDev *Wg, int64_t
 }
 
 // ---- the cell update with learned rates ------------------------------------------------------
-// 64 threads; warp w owns cells [base, base + 32): rows 0..31 dendrite (V_dend, [Ca]),
-// 32..63 soma (V_soma, [Ca]), 64..95 axon (V_axon, [Ca]); six m-tiles of 16 rows.
+// 64 threads; warp w owns CPW = 16 cells [base, base + 16): rows 0..15 dendrite (V_dend,
+// [Ca]), 16..31 soma (V_soma, [Ca]), 32..47 axon (V_axon, [Ca]); three m-tiles of 16 rows.
+// (16 rather than 32 cells per warp doubles the warps of a launch: the kernel is bound by
+// latency, not by the tensor cores.)  Lanes 0..15 then run their cells' updates.
 struct SurrArgs {
     StepCommon c;
     const MlpDev *mlp;
@@ -472,29 +474,30 @@ __device__ __forceinline__ Rate learned_rate(const float *y, int gate) {
     return Rate{learned_xinf(y, gate), ex2_approx(-y[2 * gate + 1] * 1.4426950408889634f)};
 }
 
+constexpr int SURR_CPW = 16;   // cells per warp
+
 __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
     __shared__ __align__(16) MlpDev W;
-    __shared__ float ys[2][96][MO + 1];
+    __shared__ float ys[2][3 * SURR_CPW][MO + 1];
     const StepCommon &c = a.c;
     load_mlp(W, a.mlp);
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
-    const int64_t base = ((int64_t)blockIdx.x * 2 + warp) * 32;
+    const int64_t base = ((int64_t)blockIdx.x * 2 + warp) * SURR_CPW;
     const int64_t tstep = step_index(c);
     const float *vcur = vd_cur(c, tstep);
     float *vnext = vd_next(c, tstep);
     __syncthreads();
 #pragma unroll 1
-    for (int mt = 0; mt < 6; ++mt) {
-        const int comp = mt >> 1;            // 0 dendrite, 1 soma, 2 axon
-        const int cell_lo = (mt & 1) * 16;
-        const int64_t ia = base + cell_lo + g, ib = ia + 8;
+    for (int mt = 0; mt < 3; ++mt) {
+        const int comp = mt;                 // 0 dendrite, 1 soma, 2 axon
+        const int64_t ia = base + g, ib = ia + 8;
         const float *vsrc = comp == 0 ? vcur : c.S.f(comp == 1 ? F_VSOMA : F_VAXON);
         const float va = ia < c.n ? vsrc[ia] : -60.0f, vb = ib < c.n ? vsrc[ib] : -60.0f;
         const float ca_a = ia < c.n ? c.S.f(F_CA)[ia] : 1.0f, ca_b = ib < c.n ? c.S.f(F_CA)[ib] : 1.0f;
         float y[3][4];
         mlp_mtile(W, (va - W.in_shift[0]) * W.in_scale[0], (logf(ca_a) - W.in_shift[1]) * W.in_scale[1],
                   (vb - W.in_shift[0]) * W.in_scale[0], (logf(ca_b) - W.in_shift[1]) * W.in_scale[1], y);
-        const int row = comp * 32 + cell_lo + g;
+        const int row = comp * SURR_CPW + g;
 #pragma unroll
         for (int nt = 0; nt < 3; ++nt) {
             const int o = 8 * nt + 2 * t;
@@ -506,9 +509,9 @@ __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
     }
     __syncwarp();
     const int64_t i = base + lane;
-    if (i >= c.n) return;
+    if (lane >= SURR_CPW || i >= c.n) return;
     const Cell cell = load_cell(c.S, vcur, i);
-    const float *yd = ys[warp][lane], *ysm = ys[warp][32 + lane], *yax = ys[warp][64 + lane];
+    const float *yd = ys[warp][lane], *ysm = ys[warp][SURR_CPW + lane], *yax = ys[warp][2 * SURR_CPW + lane];
     CellRates gr;
     gr.r = learned_rate(yd, G_R);
     gr.s = learned_rate(yd, G_S);
@@ -769,7 +772,7 @@ static cudaError_t surrogate_step(ion_sim *s, int k_off, const float *iapp) {
     }
     if (e != cudaSuccess) return e;
     SurrArgs sa{c, (const MlpDev *)s->d_mlp, s->kind == ION_NO_GJ ? nullptr : s->d_ic};
-    surrogate_cell_kernel<<<(unsigned)((s->n + 63) / 64), 64, 0, s->st>>>(sa);
+    surrogate_cell_kernel<<<(unsigned)((s->n + 2 * SURR_CPW - 1) / (2 * SURR_CPW)), 64, 0, s->st>>>(sa);
     s->launches++;
     return cudaGetLastError();
 }

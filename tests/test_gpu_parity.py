@@ -553,3 +553,32 @@ def test_trace_async_drain_matches_sync_read(torch_cuda, O):
                 outs.append(np.concatenate(parts))
     np.testing.assert_array_equal(outs[0], outs[1])
     assert len(O.spike_steps(outs[0][:, 0])) >= 2       # the drained trace holds real spikes
+
+
+# ------------------------------------------------------------------ the configuration the bench times
+
+@pytest.mark.parametrize("workload", ["c2", "c3_k100"])
+def test_autotuned_full_size_one_step(torch_cuda, O, workload):
+    """The full-size network after ion_autotune (as bench.py runs it: graph replay of 100
+    steps), one step from an identical warmed state against the FP64 oracle."""
+    cfg = inputs.config("c2") if workload == "c2" else inputs.config("c3", k=100)
+    n = cfg["n"]
+    S0 = initial_state(O, cfg)
+    dense = cfg["kind"] == "dense"
+    kind = O.DENSE if dense else O.CSR
+    kw = dict(g=cfg["g"]) if dense else dict(row_ptr=cfg["row_ptr"], col=cfg["col"], w=cfg["w"])
+    wd = None if dense else cfg["w"].astype(np.float64)
+    Sw, _ = O.run(S0.astype(np.float64), 3, kind=kind, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"),
+                  col=cfg.get("col"), w=wd, threads=_threads(O))
+    Sw32 = Sw.astype(np.float32)
+    ref, _ = O.run(Sw32.astype(np.float64), 1, kind=kind, g=cfg.get("g", 0.0), row_ptr=cfg.get("row_ptr"),
+                   col=cfg.get("col"), w=wd, t0=3, threads=_threads(O))
+    with ion.Simulation(n, ion.DENSE_UNIFORM if dense else ion.CSR, init_state=Sw32, graph_steps=100, **kw) as sim:
+        table = ion.ion_autotune(sim.h, 10)
+        assert sim.t == 0
+        ion.ion_set_step_count(sim.h, 3)
+        sim.step(1)
+        got = sim.state()
+    scale = cfg["g"] * sum_abs_dv(Sw32[0]) if dense else csr_abs_scale(cfg["row_ptr"], cfg["col"], cfg["w"], Sw32[0])
+    err = step_rel_err(got, ref, scale)
+    assert err.max() <= STEP_RTOL, (table, err.max(axis=1))
