@@ -82,14 +82,23 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
+            // the weights of the next group are requested before this group is computed
+            float4 wn[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                wn[r] = m0 < n4 ? __ldcs(reinterpret_cast<const float4 *>(wrow[r] + j0) + m0) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 4
             for (int mm = 0; mm < BLK; ++mm) {
                 const int mq = m0 + mm * 32;
                 if (mq < n4) {
                     float4 w4[R];
 #pragma unroll
-                    for (int r = 0; r < R; ++r)
-                        w4[r] = __ldcs(reinterpret_cast<const float4 *>(wrow[r] + j0) + mq);
+                    for (int r = 0; r < R; ++r) w4[r] = wn[r];
+                    if (mm + 1 < BLK && mq + 32 < n4) {
+#pragma unroll
+                        for (int r = 0; r < R; ++r)
+                            wn[r] = __ldcs(reinterpret_cast<const float4 *>(wrow[r] + j0) + mq + 32);
+                    }
                     const float4 v = t4[mq];
                     const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
 #pragma unroll
