@@ -102,9 +102,9 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
         }
         // order this thread's generic accesses of the buffer before any later bulk refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();   // every thread is done with this buffer
-        if (src != nullptr && threadIdx.x == 0 && kt + 2 < sm.n_tiles) {
-            issue_tile(sm, src, n_pad, kt + 2, bar);
+        if (src != nullptr && kt + 2 < sm.n_tiles) {   // refilled now: every thread must be done with it
+            __syncthreads();
+            if (threadIdx.x == 0) issue_tile(sm, src, n_pad, kt + 2, bar);
         }
     }
 #pragma unroll
@@ -134,10 +134,11 @@ __device__ __forceinline__ float gj_reduce(const DenseSmem &sm, const float (&to
         red_c[warp] = Uc;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.0f, cc = 0.0f;
-        for (int w = 0; w < W; ++w) kahan_add(s, cc, red_s[w] - red_c[w]);
-        *U_sh = s - cc;
+    if (warp == 0) {   // the warps' compensated partial sums, combined by a fixed butterfly
+        float v = lane < W ? red_s[lane] - red_c[lane] : 0.0f;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) *U_sh = v;
     }
     __syncthreads();
     return *U_sh;
