@@ -503,10 +503,10 @@ def main():
         achieved = bytes_step / per_step_s / 1e9
         peak = hbm_peak()
         roof = {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                "traffic": None, "kernel": "sgj_dense_update_kernel (+ sgj_partial_kernel)",
+                "traffic": None, "kernel": "sgj_dense_update_kernel",
                 "algorithmic_bytes_per_timestep": bytes_step, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                 "us_per_timestep": per_step_s * 1e6,
-                "note": "latency-bound: two short launches per step on an L2-resident state"}
+                "note": "latency-bound: one short launch per step on an L2-resident state"}
         extra = {"pair_evals_per_s": value * n}
     elif dense:
         # SFU-bound: one ex2 per pair evaluation (N^2 per time step); the half-work kernel

@@ -525,7 +525,7 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         if (st3 != ION_OK) return fail(st3);
     }
     if ((s->flags & ION_FLAG_SGJ) && s->kind == ION_DENSE_UNIFORM) {
-        s->lps = 2;   // partial sums + update
+        s->lps = s->n <= SGJ_ONE_LAUNCH ? 1 : 2;   // (partial sums +) update
         e = cudaMalloc(&s->d_sgj, (size_t)sgj_partials(s->n) * sizeof(float));
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
     }
@@ -670,7 +670,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
     if (s->flags & ION_FLAG_SGJ) {   // linear junctions (SGJ use case)
         if (s->kind == ION_DENSE_UNIFORM) {
             e = launch_sgj_dense_step(c, s->g, s->d_sgj, s->st);
-            s->launches += 2;
+            s->launches += s->lps;
         } else {
             CsrArgs a{};
             a.c = c;

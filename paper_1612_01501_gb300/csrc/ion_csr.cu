@@ -271,9 +271,10 @@ cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, 
 // ---- simplified gap junctions (SGJ use case, Sec. 2.3.2) ---------------------------------
 // Each connection contributes w (V_i - V_j) (the small-dV limit of the RGJ term).
 // Dense: Ic_i = g sum_j (V_i - V_j) = g (N (V_i - m) - sum_j (V_j - m)), m = V_dend of cell 0
-// (shifted so nearly equal voltages do not cancel).  Two launches per step: P CTAs write
-// Kahan partial sums of V_j - m over fixed strided ranges, then every CTA of the update
-// sums the P partials in index order and updates its cells (deterministic).
+// (shifted so nearly equal voltages do not cancel).  Larger networks take two launches
+// per step: P CTAs write Kahan partial sums of V_j - m over fixed strided ranges, then
+// every CTA of the update sums the P partials in index order and updates its cells
+// (deterministic).
 __global__ void __launch_bounds__(256) sgj_partial_kernel(const StepCommon c, float *part) {
     __shared__ float red[8];
     const int64_t t = step_index(c);
@@ -293,13 +294,30 @@ __global__ void __launch_bounds__(256) sgj_partial_kernel(const StepCommon c, fl
         part[blockIdx.x] = tot;
     }
 }
+// part == NULL (networks of at most SGJ_ONE_LAUNCH cells): every CTA sums V_j - m over all
+// cells itself, in one fixed order (the same in every CTA), so one launch does the step.
 __global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon c, const float *part, int n_part,
                                                                float g) {
     __shared__ float U_sh;
+    __shared__ float red[8];
     const int64_t t = step_index(c);
     const float *vcur = vd_cur(c, t);
     float *vnext = vd_next(c, t);
-    if (threadIdx.x == 0) {
+    if (part == nullptr) {
+        const float m0 = vcur[0];
+        float s = 0.0f, cc = 0.0f;
+        for (int64_t j = threadIdx.x; j < c.n; j += blockDim.x) kahan_add(s, cc, vcur[j] - m0);
+        float v = s - cc;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.0f;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+            U_sh = tot;
+        }
+    } else if (threadIdx.x == 0) {
         float s = 0.0f, cc = 0.0f;
         for (int q = 0; q < n_part; ++q) kahan_add(s, cc, part[q]);
         U_sh = s - cc;
@@ -316,6 +334,10 @@ __global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon 
     finish_cell(c, t, vnext, i, o);
 }
 cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st) {
+    if (c.n <= SGJ_ONE_LAUNCH) {
+        sgj_dense_update_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, nullptr, 0, g);
+        return cudaGetLastError();
+    }
     const int n_part = sgj_partials(c.n);
     sgj_partial_kernel<<<n_part, 256, 0, st>>>(c, part);
     cudaError_t e = cudaGetLastError();

@@ -122,6 +122,7 @@ cudaError_t prepare_matrix_step(int n_pad);
 cudaError_t launch_matrix_step(const MatrixArgs &a, int R, cudaStream_t st);   // R: rows per warp, 1, 2 or 4
 int matrix_default_R(int n, int sms);
 int sgj_partials(int n);   // CTAs of the SGJ partial-sum launch (the update reads that many)
+constexpr int SGJ_ONE_LAUNCH = 16384;   // SGJ dense networks up to this size take one launch per step
 cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st);
 cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st);
 cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st);

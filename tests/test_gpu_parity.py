@@ -442,7 +442,7 @@ def _sgj_one_step(O, n, kind, g=0.0, rp=None, col=None, w=None):
     return step_rel_err(got, ref, scale)
 
 
-@pytest.mark.parametrize("n", [1, 300, 8192])
+@pytest.mark.parametrize("n", [1, 300, 8192, 20000])     # up to 16 384 cells: one launch per step; 20 000: two
 def test_sgj_dense_one_step(torch_cuda, O, n):
     err = _sgj_one_step(O, n, O.DENSE, g=float(np.float32(inputs.junction_weight(0.04, n))))
     assert err.max() <= STEP_RTOL, err.max(axis=1)
