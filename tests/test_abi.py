@@ -55,6 +55,8 @@ def test_invalid_arguments_rejected(L):
     bad = ion.ion_model_default()
     bad[1] = 1.5    # p1 outside (0, 1)
     assert _create_err(n=10, kind=ion.DENSE_UNIFORM, g=0.1, model=bad) == ion.ERR_INVALID_ARG
+    # an oversize network is an error code, not an abort
+    assert _create_err(n=(1 << 28) + 1, kind=ion.NO_GJ) == ion.ERR_INVALID_ARG
     # the SGJ use case needs junctions and excludes the persistent, surrogate and split paths
     assert _create_err(n=10, kind=ion.NO_GJ, flags=ion.FLAG_SGJ) == ion.ERR_UNSUPPORTED
     assert _create_err(n=10, kind=ion.DENSE_UNIFORM, g=0.1,

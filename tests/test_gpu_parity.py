@@ -582,3 +582,27 @@ def test_autotuned_full_size_one_step(torch_cuda, O, workload):
     scale = cfg["g"] * sum_abs_dv(Sw32[0]) if dense else csr_abs_scale(cfg["row_ptr"], cfg["col"], cfg["w"], Sw32[0])
     err = step_rel_err(got, ref, scale)
     assert err.max() <= STEP_RTOL, (table, err.max(axis=1))
+
+
+# ------------------------------------------------------------------ resources
+
+def test_create_destroy_loop_does_not_leak(torch_cuda, O):
+    """Twenty create/step/destroy cycles of a dense, a CSR (compact and staged) and a
+    matrix network leave the device's free memory where it was (within 64 MB)."""
+    torch = torch_cuda
+    rp, col = inputs.random_symmetric_csr(40000, 300, 3)
+    w = np.full(len(col), inputs.junction_weight(0.04, 300), np.float32)
+    W = np.full((2048, 2048), 1e-4, np.float32)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(20):
+        for make in (lambda: ion.Simulation(8192, ion.DENSE_UNIFORM, g=3e-4),
+                     lambda: ion.Simulation(40000, ion.CSR, row_ptr=rp, col=col, w=w, tune=dict(csr_staging=2)),
+                     lambda: ion.Simulation(2048, ion.DENSE_MATRIX, w=W)):
+            with make() as sim:
+                ion.ion_set_trace(sim.h, 1, 8)
+                sim.step(3)
+                sim.sync()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free0 - free1 <= 64 << 20, (free0 - free1) / 2**20

@@ -136,3 +136,31 @@ def test_learned_rates_spiking(trained, O):
     # within about a millisecond (20 steps) on average
     assert sum(same) >= 48, sum(same)
     assert len(dstep) and dstep.mean() <= 20.0, dstep.mean() if len(dstep) else None
+
+
+def test_surrogate_gain_is_reported(trained, O):
+    """What the learned rate functions gain on this GPU: both paths time the same 4096-cell
+    network (the ratio is printed; the exact rate functions are cheap on the SFU, so the
+    surrogate is not expected to be faster here)."""
+    import time
+    w, _ = trained
+    n = 4096
+    rp, col = inputs.random_symmetric_csr(n, 100, 2)
+    wts = np.full(len(col), inputs.junction_weight(0.04, 100), np.float32)
+    S0 = O.default_state(n)
+    S0[0] += inputs.vdend_jitter(n, 2)
+    S0 = S0.astype(np.float32)
+    rate = {}
+    for name, flags, kw in (("exact", ion.FLAG_KAHAN, {}),
+                            ("surrogate", ion.FLAG_KAHAN | ion.FLAG_SURROGATE, dict(surrogate=w))):
+        with ion.Simulation(n, ion.CSR, row_ptr=rp, col=col, w=wts, init_state=S0, flags=flags, **kw) as sim:
+            sim.step(200)
+            sim.sync()
+            t0 = time.perf_counter()
+            sim.step(2000)
+            sim.sync()
+            rate[name] = n * 2000 / (time.perf_counter() - t0)
+            assert np.all(np.isfinite(sim.state()))
+    print(f"cell-steps/s: exact {rate['exact']:.3e}, surrogate {rate['surrogate']:.3e}, "
+          f"gain {rate['surrogate'] / rate['exact']:.2f}x")
+    assert rate["exact"] > 0 and rate["surrogate"] > 0
