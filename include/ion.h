@@ -280,6 +280,11 @@ ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
  * pointer may be NULL. */
 ion_status ion_csr_layout(const ion_sim *sim, int32_t *index_bytes, int32_t *weight_bytes, int32_t *staged);
 
+/* Test hook, never called in production: the device allocation that follows the next
+ * `after` ones (in any handle of the process) reports out-of-memory, once, so that the
+ * error paths of creation and setup can be exercised; a negative value disarms it. */
+ion_status ion_debug_fail_alloc(int32_t after);
+
 /* Steps taken so far (the absolute index of the next step). */
 int64_t ion_step_count(const ion_sim *sim);
 

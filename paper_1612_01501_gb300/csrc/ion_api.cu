@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -57,8 +58,8 @@ ion_status ion_fail(ion_sim *s, ion_status code, const char *fmt, ...) {
     do {                                                                                       \
         cudaError_t e_ = (call);                                                               \
         if (e_ != cudaSuccess)                                                                 \
-            return ion_fail((sim), ION_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
-                            __FILE__, __LINE__);                                               \
+            return ion_fail((sim), e_ == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA,   \
+                            "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
     } while (0)
 
 ModelF ion_model_to_f32(const ion_model &m, double dt) {
@@ -124,7 +125,7 @@ extern "C" int64_t ion_launch_count(const ion_sim *s) { return s ? s->launches :
 extern "C" ion_status ion_rates(float V, float ca, float *xinf, float *tau) {
     if (!xinf || !tau) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_rates: NULL output");
     float *d = nullptr;
-    ION_CK(nullptr, cudaMalloc(&d, 2 * NG * sizeof(float)));
+    ION_CK(nullptr, ion_alloc(&d, 2 * NG * sizeof(float)));
     cudaError_t e = launch_rates(V, ca, d, 0);
     float h[2 * NG];
     if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof h, cudaMemcpyDeviceToHost);
@@ -142,13 +143,35 @@ extern "C" ion_status ion_default_state(const ion_model *model, int32_t n, float
     else ion_model_default(&m);
     if (!model_valid(m)) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_default_state: invalid model table");
     float *d = nullptr;
-    ION_CK(nullptr, cudaMalloc(&d, (size_t)NF * n * sizeof(float)));
+    ION_CK(nullptr, ion_alloc(&d, (size_t)NF * n * sizeof(float)));
     const ModelF P = ion_model_to_f32(m, 0.05);
     cudaError_t e = launch_default_state(P, (float)m.v[ION_P_V0], (float)m.v[ION_P_CA0], (float)m.v[ION_P_GCAL], n, n,
                                          d, 0);
     if (e == cudaSuccess) e = cudaMemcpy(out, d, (size_t)NF * n * sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "ion_default_state: %s", cudaGetErrorString(e));
+    return ION_OK;
+}
+
+// ---- device allocation (with the test hook) ------------------------------------------
+static std::atomic<int64_t> g_fail_after{-1};   // allocations left before the injected failure
+
+cudaError_t ion_dev_alloc(void **p, size_t bytes) {
+    int64_t k = g_fail_after.load();
+    while (k >= 0) {
+        if (g_fail_after.compare_exchange_weak(k, k - 1)) {
+            if (k == 0) {   // this call fails, once
+                *p = nullptr;
+                return cudaErrorMemoryAllocation;
+            }
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
+}
+
+extern "C" ion_status ion_debug_fail_alloc(int32_t after) {
+    g_fail_after.store(after < 0 ? -1 : (int64_t)after);
     return ION_OK;
 }
 
@@ -287,9 +310,11 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     if (s->csr_chunk_rows == 0) s->csr_chunk_rows = rows;
     s->csr_chunk_SW = sw;
     if (s->n_chunks > 1 && !s->d_mid) {
-        cudaError_t e = cudaMalloc(&s->d_mid, (size_t)(s->n_chunks - 1) * s->n * sizeof(int32_t));
+        cudaError_t e = ion_alloc(&s->d_mid, (size_t)(s->n_chunks - 1) * s->n * sizeof(int32_t));
         if (e == cudaSuccess) e = launch_csr_chunk_bounds(s->d_rowptr, s->d_col, s->n, s->n_chunks, s->d_mid, s->st);
-        if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR staging setup: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess)
+            return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "CSR staging setup: %s",
+                            cudaGetErrorString(e));
     }
     const ion_status st = ion_prepare_csr_chunk(s);
     if (st != ION_OK) return st;
@@ -410,16 +435,17 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     s->sms = sms;
 
     auto fail = [&](ion_status code) {
+        cudaStreamSynchronize(s->st);   // initialisation kernels already queued finish first
         ion_sim_free_device(s);
         if (s->own_stream) cudaStreamDestroy(s->own_stream);
         delete s;
         return code;
     };
     // state: 20 slots of stride floats (fields 0..18 + second V_dend slot)
-    cudaError_t e = cudaMalloc(&s->d_state, (size_t)20 * s->stride * sizeof(float));
+    cudaError_t e = ion_alloc(&s->d_state, (size_t)20 * s->stride * sizeof(float));
     if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: state allocation: %s", cudaGetErrorString(e)));
-    e = cudaMalloc(&s->d_t, sizeof(int64_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_status, sizeof(uint32_t));
+    e = ion_alloc(&s->d_t, sizeof(int64_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_status, sizeof(uint32_t));
     if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
     e = cudaMemsetAsync(s->d_state, 0, (size_t)20 * s->stride * sizeof(float), s->st);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_t, 0, sizeof(int64_t), s->st);
@@ -456,7 +482,7 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         e = prepare_dense_step(R, W, GJ, s->n_pad);
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: dense setup: %s", cudaGetErrorString(e)));
     } else if (s->kind == ION_DENSE_MATRIX) {
-        e = cudaMalloc(&s->d_W, (size_t)s->n * s->n_pad * sizeof(float));
+        e = ion_alloc(&s->d_W, (size_t)s->n * s->n_pad * sizeof(float));
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: matrix allocation: %s", cudaGetErrorString(e)));
         e = cudaMemsetAsync(s->d_W, 0, (size_t)s->n * s->n_pad * sizeof(float), s->st);
         if (e == cudaSuccess)
@@ -496,11 +522,11 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
                     keep_w = false;
                 }
             }
-            e = cudaMalloc(&s->d_rowptr, (size_t)(s->n + 1) * sizeof(int32_t));
-            if (e == cudaSuccess && s->nnz > 0) e = cudaMalloc(&s->d_col, (size_t)s->nnz * sizeof(int32_t));
-            if (e == cudaSuccess && keep_w) e = cudaMalloc(&s->d_w, (size_t)s->nnz * sizeof(float));
+            e = ion_alloc(&s->d_rowptr, (size_t)(s->n + 1) * sizeof(int32_t));
+            if (e == cudaSuccess && s->nnz > 0) e = ion_alloc(&s->d_col, (size_t)s->nnz * sizeof(int32_t));
+            if (e == cudaSuccess && keep_w) e = ion_alloc(&s->d_w, (size_t)s->nnz * sizeof(float));
             // the low 16 bits of every column, padded to whole 16-byte groups
-            if (e == cudaSuccess && s->nnz > 0 && compact) e = cudaMalloc(&s->d_col16, (size_t)round_up(s->nnz, 8) * sizeof(uint16_t));
+            if (e == cudaSuccess && s->nnz > 0 && compact) e = ion_alloc(&s->d_col16, (size_t)round_up(s->nnz, 8) * sizeof(uint16_t));
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: CSR allocation: %s", cudaGetErrorString(e)));
             e = cudaMemcpyAsync(s->d_rowptr, conn->row_ptr, (size_t)(s->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
             if (e == cudaSuccess && s->nnz > 0)
@@ -526,12 +552,12 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     }
     if ((s->flags & ION_FLAG_SGJ) && s->kind == ION_DENSE_UNIFORM) {
         s->lps = s->n <= SGJ_ONE_LAUNCH ? 1 : 2;   // (partial sums +) update
-        e = cudaMalloc(&s->d_sgj, (size_t)sgj_partials(s->n) * sizeof(float));
+        e = ion_alloc(&s->d_sgj, (size_t)sgj_partials(s->n) * sizeof(float));
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
     }
     if ((s->flags & ION_FLAG_SPLIT) && s->kind != ION_NO_GJ) {
         s->lps = 2;
-        e = cudaMalloc(&s->d_ic, (size_t)s->n_pad * sizeof(float));
+        e = ion_alloc(&s->d_ic, (size_t)s->n_pad * sizeof(float));
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
     }
     ion_status st2 = ion_sim_setup_extras(s, params);
@@ -606,14 +632,25 @@ static ion_status install_pulses(ion_sim *s, const ion_input *in) {
         s->gexec = nullptr;
     }
     if (np == 0) return ION_OK;
-    ION_CK(s, cudaMalloc(&s->d_poff, (s->n + 1) * sizeof(int32_t)));
-    ION_CK(s, cudaMalloc(&s->d_pbeg, np * sizeof(int64_t)));
-    ION_CK(s, cudaMalloc(&s->d_pend, np * sizeof(int64_t)));
-    ION_CK(s, cudaMalloc(&s->d_pamp, np * sizeof(float)));
-    ION_CK(s, cudaMemcpy(s->d_poff, off.data(), (s->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
-    ION_CK(s, cudaMemcpy(s->d_pbeg, b2.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice));
-    ION_CK(s, cudaMemcpy(s->d_pend, e2.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice));
-    ION_CK(s, cudaMemcpy(s->d_pamp, a2.data(), np * sizeof(float), cudaMemcpyHostToDevice));
+    cudaError_t e = ion_alloc(&s->d_poff, (s->n + 1) * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_pbeg, np * sizeof(int64_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_pend, np * sizeof(int64_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_pamp, np * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_poff, off.data(), (s->n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_pbeg, b2.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_pend, e2.data(), np * sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_pamp, a2.data(), np * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {   // leave no half-built table behind: the kernels would read it
+        cudaFree(s->d_poff);
+        cudaFree(s->d_pbeg);
+        cudaFree(s->d_pend);
+        cudaFree(s->d_pamp);
+        s->d_poff = nullptr;
+        s->d_pbeg = s->d_pend = nullptr;
+        s->d_pamp = nullptr;
+        return ion_fail(s, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_set_input: %s",
+                        cudaGetErrorString(e));
+    }
     s->n_pulses = np;
     return ION_OK;
 }
@@ -640,7 +677,7 @@ StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp) {
     c.t_dev = s->d_t;
     c.k_off = k_off;
     c.vd_fixed = 0;
-    c.pulses.off = s->d_poff;
+    c.pulses.off = s->n_pulses > 0 ? s->d_poff : nullptr;   // no table unless one is complete
     c.pulses.begin = s->d_pbeg;
     c.pulses.end = s->d_pend;
     c.pulses.amp = s->d_pamp;
@@ -784,7 +821,7 @@ extern "C" ion_status ion_step(ion_sim *s, int64_t n_steps, const ion_input *inp
                 cudaFree(s->d_iapp);
                 s->d_iapp = nullptr;
                 s->iapp_cap = 0;
-                ION_CK(s, cudaMalloc(&s->d_iapp, (size_t)cnt * sizeof(float)));
+                ION_CK(s, ion_alloc(&s->d_iapp, (size_t)cnt * sizeof(float)));
                 s->iapp_cap = cnt;
             }
             ION_CK(s, cudaMemcpyAsync(s->d_iapp, input->dense, (size_t)cnt * sizeof(float), cudaMemcpyHostToDevice, s->st));
@@ -947,7 +984,7 @@ extern "C" ion_status ion_set_trace(ion_sim *s, int32_t stride, int32_t capacity
         s->gexec = nullptr;
     }
     if (stride == 0 || capacity == 0) return ION_OK;
-    ION_CK(s, cudaMalloc(&s->d_trace, (size_t)capacity * s->n * sizeof(float)));
+    ION_CK(s, ion_alloc(&s->d_trace, (size_t)capacity * s->n * sizeof(float)));
     s->trace_stride = stride;
     s->trace_cap = capacity;
     s->trace_read = s->t / stride;
@@ -1099,7 +1136,7 @@ extern "C" ion_status ion_cell_update(float *state, int32_t n, const float *ic, 
     a.ic = ic;
     // the status word is not reported by this primitive: point it at a private word
     static uint32_t *d_dummy = nullptr;
-    if (!d_dummy) ION_CK(nullptr, cudaMalloc(&d_dummy, sizeof(uint32_t)));
+    if (!d_dummy) ION_CK(nullptr, ion_alloc(&d_dummy, sizeof(uint32_t)));
     a.c.status = d_dummy;
     cudaError_t e = launch_cell_step(a, (cudaStream_t)stream);
     if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "ion_cell_update: %s", cudaGetErrorString(e));

@@ -295,17 +295,19 @@ static ion_status batch_plan(ion_sim *s) {
     std::vector<BatchTile> sorted(tiles.size());
     for (size_t k = 0; k < order.size(); ++k) sorted[k] = tiles[order[k]];
     cudaError_t e = cudaStreamSynchronize(s->st);
-    if (e == cudaSuccess && X->d_tiles) e = cudaFree(X->d_tiles);
-    X->d_tiles = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&X->d_tiles, std::max<size_t>(1, sorted.size()) * sizeof(BatchTile));
-    if (e == cudaSuccess)
-        e = cudaMemcpy(X->d_tiles, sorted.data(), sorted.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "batch plan: %s", cudaGetErrorString(e));
-    X->n_tiles = (int)sorted.size();
-    if (s->gexec) {
+    if (s->gexec) {   // the captured steps hold the old tile list
         cudaGraphExecDestroy(s->gexec);
         s->gexec = nullptr;
     }
+    if (e == cudaSuccess && X->d_tiles) e = cudaFree(X->d_tiles);
+    X->d_tiles = nullptr;   // until a new list is in place, stepping is refused
+    X->n_tiles = 0;
+    if (e == cudaSuccess) e = ion_alloc(&X->d_tiles, std::max<size_t>(1, sorted.size()) * sizeof(BatchTile));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(X->d_tiles, sorted.data(), sorted.size() * sizeof(BatchTile), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return ion_fail(s, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "batch plan: %s", cudaGetErrorString(e));
+    X->n_tiles = (int)sorted.size();
     return ION_OK;
 }
 
@@ -330,6 +332,7 @@ static cudaError_t batch_launch(const BatchArgs &a, int R, int tiles, size_t sme
 
 static cudaError_t batch_step(ion_sim *s, int k_off, const float *iapp) {
     BatchExt *X = ext_of(s);
+    if (X->d_tiles == nullptr) return cudaErrorInvalidResourceHandle;   // no tile list: a failed re-plan
     BatchArgs a{};
     a.c = ion_step_common(s, k_off, iapp);
     a.tiles = X->d_tiles;
@@ -517,14 +520,14 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     for (size_t i = 0; i < (size_t)seg; ++i) rp[i + 1] += rp[i];
     // the per-row counts above were placed in network order, so the prefix sum lines the
     // edges up with x.e0 (segments are laid out in network order)
-    cudaError_t e = cudaMalloc(&s->d_rowptr, rp.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_col, col.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_w, w.size() * sizeof(float));
-    if (e == cudaSuccess && any16) e = cudaMalloc(&s->d_col16, col16.size() * sizeof(uint16_t));
-    if (e == cudaSuccess) e = cudaMalloc(&s->d_map, X->h_map.size() * sizeof(int32_t));
-    if (e == cudaSuccess) e = cudaMalloc(&X->d_tmp, (size_t)NF * n_user * sizeof(float));
+    s->own_csr = true;   // before the allocations, so that a partial failure frees them
+    cudaError_t e = ion_alloc(&s->d_rowptr, rp.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_col, col.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_w, w.size() * sizeof(float));
+    if (e == cudaSuccess && any16) e = ion_alloc(&s->d_col16, col16.size() * sizeof(uint16_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_map, X->h_map.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&X->d_tmp, (size_t)NF * n_user * sizeof(float));
     if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create_batch: %s", cudaGetErrorString(e)));
-    s->own_csr = true;
     s->nnz = nnz_total;
     e = cudaMemcpy(s->d_rowptr, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(s->d_col, col.data(), col.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
@@ -591,9 +594,13 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
     float *save = nullptr;
     const size_t bytes = (size_t)20 * s->stride * sizeof(float);
     cudaError_t e = cudaStreamSynchronize(s->st);
-    if (e == cudaSuccess) e = cudaMalloc(&save, bytes);
+    if (e == cudaSuccess) e = ion_alloc(&save, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(save, s->d_state, bytes, cudaMemcpyDeviceToDevice);
-    if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "ion_autotune: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess) {
+        cudaFree(save);
+        return ion_fail(s, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_autotune: %s",
+                        cudaGetErrorString(e));
+    }
     const int64_t t0 = s->t;
     auto restore = [&]() {
         cudaStreamSynchronize(s->st);

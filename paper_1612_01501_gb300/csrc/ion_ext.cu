@@ -100,8 +100,14 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
         if (coop && choose_persist_shape(s)) {
-            if (cudaMalloc(&s->d_bar, 2 * sizeof(uint32_t)) != cudaSuccess)
+            if (ion_alloc(&s->d_bar, 2 * sizeof(uint32_t)) != cudaSuccess)
                 return ion_fail(nullptr, ION_ERR_OOM, "persistent: barrier allocation failed");
+            s->extra_free = [](ion_sim *q) {   // set before any later allocation can fail
+                cudaFree(q->d_bar);
+                cudaFree(q->d_half);
+                q->d_bar = nullptr;
+                q->d_half = nullptr;
+            };
             s->run_override = persist_run;
             // several CTAs: the half-work kernel, if its shape and grid fit
             const int rows = (s->persist_W / s->persist_GJ) * s->persist_R;
@@ -115,17 +121,11 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
                     fits) {
                     s->half_grid = grid;
                     s->half_stride = half_colsum_stride(grid, rows);
-                    if (cudaMalloc(&s->d_half, ((size_t)grid * s->half_stride + grid) * sizeof(float)) != cudaSuccess)
+                    if (ion_alloc(&s->d_half, ((size_t)grid * s->half_stride + grid) * sizeof(float)) != cudaSuccess)
                         return ion_fail(nullptr, ION_ERR_OOM, "persistent: column-sum buffer allocation failed");
                     s->run_override = half_run;
                 }
             }
-            s->extra_free = [](ion_sim *q) {
-                cudaFree(q->d_bar);
-                cudaFree(q->d_half);
-                q->d_bar = nullptr;
-                q->d_half = nullptr;
-            };
         }
     }
     return ION_OK;

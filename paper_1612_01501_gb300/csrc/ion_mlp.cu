@@ -573,7 +573,7 @@ extern "C" ion_status ion_surrogate_train(const ion_train_cfg *cfg, ion_surrogat
     const int sblk = 64;
     std::vector<void *> bufs;
     auto alloc = [&](void **p, size_t bytes) {
-        cudaError_t e = cudaMalloc(p, bytes);
+        cudaError_t e = ion_alloc(p, bytes);
         if (e == cudaSuccess) bufs.push_back(*p);
         return e;
     };
@@ -663,13 +663,13 @@ extern "C" ion_status ion_surrogate_grad(const ion_surrogate_weights *w, const f
     for (int o = 0; o < MO; ++o) msum += mask[o];
     if (!(msum > 0)) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_surrogate_grad: empty mask");
     float *params = nullptr, *X = nullptr, *T = nullptr, *M = nullptr, *partial = nullptr, *g = nullptr, *L = nullptr;
-    cudaError_t e = cudaMalloc(&params, P_TOTAL * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&X, (size_t)B * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&T, (size_t)B * MO * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&M, MO * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&partial, (size_t)nblk * (P_TOTAL + 1) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&g, P_TOTAL * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&L, 4);
+    cudaError_t e = ion_alloc(&params, P_TOTAL * 4);
+    if (e == cudaSuccess) e = ion_alloc(&X, (size_t)B * 8);
+    if (e == cudaSuccess) e = ion_alloc(&T, (size_t)B * MO * 4);
+    if (e == cudaSuccess) e = ion_alloc(&M, MO * 4);
+    if (e == cudaSuccess) e = ion_alloc(&partial, (size_t)nblk * (P_TOTAL + 1) * 4);
+    if (e == cudaSuccess) e = ion_alloc(&g, P_TOTAL * 4);
+    if (e == cudaSuccess) e = ion_alloc(&L, 4);
     if (e == cudaSuccess) e = cudaMemcpy(params, w, P_TOTAL * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(X, x, (size_t)B * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(T, t, (size_t)B * MO * 4, cudaMemcpyHostToDevice);
@@ -695,7 +695,9 @@ extern "C" ion_status ion_surrogate_grad(const ion_surrogate_weights *w, const f
     cudaFree(partial);
     cudaFree(g);
     cudaFree(L);
-    if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "ion_surrogate_grad: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_surrogate_grad: %s",
+                        cudaGetErrorString(e));
     if (loss) *loss = hl;
     return ION_OK;
 }
@@ -704,8 +706,8 @@ extern "C" ion_status ion_surrogate_grad(const ion_surrogate_weights *w, const f
 ion_status ion_mlp_upload(const ion_surrogate_weights *w, void **d_out, cudaStream_t st) {
     ion_surrogate_weights *dw = nullptr;
     MlpDev *d = nullptr;
-    cudaError_t e = cudaMalloc(&dw, sizeof *dw);
-    if (e == cudaSuccess) e = cudaMalloc(&d, sizeof *d);
+    cudaError_t e = ion_alloc(&dw, sizeof *dw);
+    if (e == cudaSuccess) e = ion_alloc(&d, sizeof *d);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, sizeof *dw, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         mlp_pack_kernel<<<1, 256, 0, st>>>(dw, d);
@@ -715,7 +717,8 @@ ion_status ion_mlp_upload(const ion_surrogate_weights *w, void **d_out, cudaStre
     cudaFree(dw);
     if (e != cudaSuccess) {
         cudaFree(d);
-        return ion_fail(nullptr, ION_ERR_CUDA, "surrogate upload: %s", cudaGetErrorString(e));
+        return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "surrogate upload: %s",
+                        cudaGetErrorString(e));
     }
     *d_out = d;
     return ION_OK;
@@ -728,9 +731,9 @@ extern "C" ion_status ion_surrogate_eval(const ion_surrogate_weights *w, const f
     ion_status st = ion_mlp_upload(w, &d, nullptr);
     if (st != ION_OK) return st;
     float *dV = nullptr, *dc = nullptr, *dout = nullptr;
-    cudaError_t e = cudaMalloc(&dV, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&dc, n * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&dout, n * MO * 4);
+    cudaError_t e = ion_alloc(&dV, n * 4);
+    if (e == cudaSuccess) e = ion_alloc(&dc, n * 4);
+    if (e == cudaSuccess) e = ion_alloc(&dout, n * MO * 4);
     if (e == cudaSuccess) e = cudaMemcpy(dV, V, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dc, ca, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) {
@@ -742,7 +745,9 @@ extern "C" ion_status ion_surrogate_eval(const ion_surrogate_weights *w, const f
     cudaFree(dc);
     cudaFree(dout);
     cudaFree(d);
-    if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "ion_surrogate_eval: %s", cudaGetErrorString(e));
+    if (e != cudaSuccess)
+        return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_surrogate_eval: %s",
+                        cudaGetErrorString(e));
     return ION_OK;
 }
 
@@ -782,7 +787,7 @@ ion_status ion_setup_surrogate(ion_sim *s, const ion_params *p) {
     ion_status st = ion_mlp_upload((const ion_surrogate_weights *)p->surrogate, &s->d_mlp, s->st);
     if (st != ION_OK) return st;
     if (s->kind != ION_NO_GJ && !s->d_ic) {
-        cudaError_t e = cudaMalloc(&s->d_ic, (size_t)s->n_pad * sizeof(float));
+        cudaError_t e = ion_alloc(&s->d_ic, (size_t)s->n_pad * sizeof(float));
         if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_OOM, "surrogate: %s", cudaGetErrorString(e));
     }
     s->step_override = surrogate_step;

@@ -86,6 +86,14 @@ struct ion_sim {
     int64_t launches_per_step() const { return lps; }
 };
 
+// Device allocation of every handle buffer; a test hook (ion_debug_fail_alloc) can make one
+// call report out-of-memory so that the error paths are exercised without a real shortage.
+cudaError_t ion_dev_alloc(void **p, size_t bytes);
+template <class T>
+inline cudaError_t ion_alloc(T **p, size_t bytes) {
+    return ion_dev_alloc(reinterpret_cast<void **>(p), bytes);
+}
+
 // shared helpers (ion_api.cu)
 void ion_csr_fill(const ion_sim *s, ion::CsrArgs &a, bool staged);
 ion_status ion_prepare_csr_chunk(ion_sim *s);

@@ -110,6 +110,7 @@ _SIGS = {
     "ion_read_trace_async": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, c_i64p]),
     "ion_trace_wait": (ctypes.c_int, [ctypes.c_void_p]),
     "ion_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "ion_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
     "ion_csr_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     "ion_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ion_tune)]),
@@ -389,6 +390,11 @@ def ion_csr_layout(h) -> dict:
     ib, wb, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().ion_csr_layout(h, ctypes.byref(ib), ctypes.byref(wb), ctypes.byref(st)), h)
     return {"index_bytes": ib.value, "weight_bytes": wb.value, "staged": st.value}
+
+
+def ion_debug_fail_alloc(after: int):
+    """Test hook: make the device allocation after the next `after` ones fail once (-1 disarms)."""
+    lib().ion_debug_fail_alloc(int(after))
 
 
 def ion_step_count(h) -> int:
