@@ -430,7 +430,8 @@ def main():
         sim.sync()                                      # the run stayed finite
         return sim, ms, launches, ck, tune_table
 
-    cand = [("graph", ion.FLAG_KAHAN)]
+    cand = [("graph", ion.FLAG_KAHAN),
+            ("graph_ordinary_launches", ion.FLAG_KAHAN | ion.FLAG_NO_PDL)]   # without programmatic launches
     if dense and not wl.get("sgj"):
         cand.append(("persistent", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT))
         if n > 144:   # multi-CTA networks: the half-work pass as well as the full pass

@@ -100,9 +100,15 @@ enum ion_flag {
                                       L2 (two bounded barriers per step)                     */
     ION_FLAG_CSR_AS_GIVEN = 1u << 7, /* CSR: keep 32-bit columns and per-edge weights even when
                                       a compact layout applies (see ion_csr_layout)         */
-    ION_FLAG_SGJ = 1u << 8         /* SGJ use case (Sec. 2.3.2): each connection contributes
+    ION_FLAG_SGJ = 1u << 8,        /* SGJ use case (Sec. 2.3.2): each connection contributes
                                       w (V_i - V_j) instead of the RGJ term.  Dense or CSR;
                                       not with PERSISTENT, SURROGATE, SPLIT or batches      */
+    ION_FLAG_NO_PDL = 1u << 9      /* launch the per-step kernels as ordinary stream-ordered
+                                      launches.  By default each is launched with programmatic
+                                      stream serialization: its CTAs may be scheduled while the
+                                      previous step's kernel drains, and wait on the device
+                                      (griddepcontrol.wait) for its completion before touching
+                                      memory.  Results are identical either way.             */
 };
 
 typedef struct {

@@ -686,6 +686,7 @@ StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp) {
     c.trace = s->d_trace;
     c.trace_stride = s->trace_stride;
     c.trace_cap = s->trace_cap;
+    c.pdl = !(s->flags & ION_FLAG_NO_PDL) && !s->pdl_off;
     c.P = s->P;
     return c;
 }
@@ -778,7 +779,7 @@ static cudaError_t enqueue_steps_direct(ion_sim *s, int64_t k, const float *iapp
     return cudaSuccess;
 }
 
-static ion_status build_graph(ion_sim *s) {
+static ion_status build_graph_once(ion_sim *s) {
     const int K = s->graph_steps;
     cudaGraph_t g = nullptr;
     const int64_t launches0 = s->launches;
@@ -800,6 +801,16 @@ static ion_status build_graph(ion_sim *s) {
     }
     s->graph_launches = (int64_t)K * s->launches_per_step() + 1;   // + the counter advance
     return ION_OK;
+}
+
+// Capture the K-step graph; if a capture with programmatic launches is refused, capture
+// again with ordinary launches (and keep them for this handle).
+static ion_status build_graph(ion_sim *s) {
+    ion_status st = build_graph_once(s);
+    if (st == ION_OK || (s->flags & ION_FLAG_NO_PDL) || s->pdl_off) return st;
+    (void)cudaGetLastError();
+    s->pdl_off = true;
+    return build_graph_once(s);
 }
 
 extern "C" ion_status ion_step(ion_sim *s, int64_t n_steps, const ion_input *input) {

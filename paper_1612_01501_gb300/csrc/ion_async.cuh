@@ -26,6 +26,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
         : "memory");
     return ok != 0;
 }
+// Programmatic dependent launch (griddepcontrol, sm_90+).  A kernel launched with
+// programmatic stream serialization may be scheduled while the kernel before it in the
+// stream is still draining.  pdl_enter() first waits until that kernel has completed and
+// its writes are visible (at once for an ordinary launch), then allows the next kernel
+// launched that way to be scheduled.  Every kernel so launched calls it before its first
+// global-memory access.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

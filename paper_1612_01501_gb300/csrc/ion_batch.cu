@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
     __shared__ float red_s[32], red_c[32];
     __shared__ float U_sh;
     __shared__ float ic_s[256];
+    pdl_enter();
 
     const BatchTile T = a.tiles[blockIdx.x];
     const StepCommon &c = a.c;
@@ -317,8 +318,7 @@ template <int R>
 static cudaError_t batch_launch_R(const BatchArgs &a, int tiles, size_t smem, cudaStream_t st, bool prepare) {
     if (prepare)
         return cudaFuncSetAttribute(batch_step_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    batch_step_kernel<R><<<tiles, 256, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(batch_step_kernel<R>, dim3(tiles), dim3(256), smem, st, a.c.pdl != 0, a);
 }
 static cudaError_t batch_launch(const BatchArgs &a, int R, int tiles, size_t smem, cudaStream_t st, bool prepare) {
     switch (R) {

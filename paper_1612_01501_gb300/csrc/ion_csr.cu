@@ -25,6 +25,7 @@ namespace ion {
 template <int SW, bool VEC, bool HAS_W, bool C16>
 __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows) {
     __shared__ float ic_s[256];
+    pdl_enter();
     const StepCommon &c = a.c;
     const int n = c.n;
     const int row0 = blockIdx.x * rows;
@@ -67,8 +68,7 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
 template <int SW, bool VEC, bool HAS_W, bool C16 = false>
 static cudaError_t launch_csr_T(const CsrArgs &a, int rows, cudaStream_t st) {
     const int grid = (a.c.n + rows - 1) / rows;
-    csr_step_kernel<SW, VEC, HAS_W, C16><<<grid, 256, 0, st>>>(a, rows);
-    return cudaGetLastError();
+    return launch_k(csr_step_kernel<SW, VEC, HAS_W, C16>, dim3(grid), dim3(256), 0, st, a.c.pdl != 0, a, rows);
 }
 template <int SW>
 static cudaError_t launch_csr_SW(const CsrArgs &a, int rows, cudaStream_t st) {
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
     float *vs = reinterpret_cast<float *>(smem_raw);
     float *ic_s = vs + min(CSR_CHUNK, a.c.n_pad);
     __shared__ __align__(8) uint64_t bar;
-    __shared__ int ok_sh;
+    pdl_enter();
     const StepCommon &c = a.c;
     const int n = c.n;
     const int row0 = blockIdx.x * rows;
@@ -203,8 +203,8 @@ static cudaError_t chunk_T(const CsrArgs &a, int rows, const int32_t *mid, int n
         return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (a.c.n + rows - 1) / rows;
-    csr_chunk_step_kernel<SW, VEC, HAS_W, C16><<<grid, 1024, smem, st>>>(a, rows, mid, n_chunks);
-    return cudaGetLastError();
+    return launch_k(csr_chunk_step_kernel<SW, VEC, HAS_W, C16>, dim3(grid), dim3(1024), smem, st, a.c.pdl != 0, a,
+                    rows, mid, n_chunks);
 }
 template <int SW>
 static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
@@ -277,6 +277,7 @@ cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, 
 // (deterministic).
 __global__ void __launch_bounds__(256) sgj_partial_kernel(const StepCommon c, float *part) {
     __shared__ float red[8];
+    pdl_enter();
     const int64_t t = step_index(c);
     const float *vcur = vd_cur(c, t);
     const float m = vcur[0];
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon 
                                                                float g) {
     __shared__ float U_sh;
     __shared__ float red[8];
+    pdl_enter();
     const int64_t t = step_index(c);
     const float *vcur = vd_cur(c, t);
     float *vnext = vd_next(c, t);
@@ -335,21 +337,21 @@ __global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon 
 }
 cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st) {
     if (c.n <= SGJ_ONE_LAUNCH) {
-        sgj_dense_update_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, nullptr, 0, g);
-        return cudaGetLastError();
+        return launch_k(sgj_dense_update_kernel, dim3((c.n + 255) / 256), dim3(256), 0, st, c.pdl != 0, c,
+                        (const float *)nullptr, 0, g);
     }
     const int n_part = sgj_partials(c.n);
-    sgj_partial_kernel<<<n_part, 256, 0, st>>>(c, part);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(sgj_partial_kernel, dim3(n_part), dim3(256), 0, st, c.pdl != 0, c, part);
     if (e != cudaSuccess) return e;
-    sgj_dense_update_kernel<<<(unsigned)((c.n + 255) / 256), 256, 0, st>>>(c, part, n_part, g);
-    return cudaGetLastError();
+    return launch_k(sgj_dense_update_kernel, dim3((c.n + 255) / 256), dim3(256), 0, st, c.pdl != 0, c,
+                    (const float *)part, n_part, g);
 }
 int sgj_partials(int n) { return std::min(256, std::max(1, (n + 4095) / 4096)); }
 
 // CSR: eight lanes per row, 32 rows per CTA, then the cell update of the CTA's rows.
 __global__ void __launch_bounds__(256) sgj_csr_step_kernel(const CsrArgs a) {
     __shared__ float ic_s[32];
+    pdl_enter();
     const StepCommon &c = a.c;
     const int64_t t = step_index(c);
     const float *vcur = vd_cur(c, t);
@@ -378,8 +380,7 @@ __global__ void __launch_bounds__(256) sgj_csr_step_kernel(const CsrArgs a) {
     finish_cell(c, t, vnext, r, o);
 }
 cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st) {
-    sgj_csr_step_kernel<<<(unsigned)((a.c.n + 31) / 32), 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(sgj_csr_step_kernel, dim3((a.c.n + 31) / 32), dim3(256), 0, st, a.c.pdl != 0, a);
 }
 
 // ---- compact column layout: the low 16 bits of every column (zero padding to 8 entries)
@@ -395,6 +396,7 @@ cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, u
 
 // ---- stand-alone cell update (no gap junctions, or Ic computed by another launch) ----
 __global__ void __launch_bounds__(256) cell_step_kernel(const CellArgs a) {
+    pdl_enter();
     const StepCommon &c = a.c;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.n) return;
@@ -411,8 +413,7 @@ __global__ void __launch_bounds__(256) cell_step_kernel(const CellArgs a) {
 
 cudaError_t launch_cell_step(const CellArgs &a, cudaStream_t st) {
     const int64_t grid = ((int64_t)a.c.n + 255) / 256;
-    cell_step_kernel<<<(unsigned)grid, 256, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_k(cell_step_kernel, dim3((unsigned)grid), dim3(256), 0, st, a.c.pdl != 0, a);
 }
 
 // ---- rate functions and default state (host-visible copies of the device model) ----

@@ -51,21 +51,21 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     const int rg = warp % GR, cs = warp / GR;
     const int rows_cta = GR * R;
     const DenseSmem sm = dense_smem(smem_raw, c.n_pad);
-
-    const int64_t t = step_index(c);
-    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
-    float *vnext = a.fuse ? vd_next(c, t) : nullptr;
-    const int row_base = blockIdx.x * rows_cta;
-    const float m_shift = vcur[0];
-
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    pdl_enter();
+
+    const int64_t t = step_index(c);
+    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
+    float *vnext = a.fuse ? vd_next(c, t) : nullptr;
+    const int row_base = blockIdx.x * rows_cta;
     __syncthreads();
     if (threadIdx.x == 0)
         for (int k = 0; k < 2 && k < sm.n_tiles; ++k) issue_tile(sm, vcur, c.n_pad, k, bar);
+    const float m_shift = vcur[0];
 
     float ui[R];
 #pragma unroll
@@ -276,8 +276,7 @@ struct StepOp {
         if (L.prepare_only)
             return cudaFuncSetAttribute(dense_step_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = (L.a->c.n + rows_cta - 1) / rows_cta;
-        dense_step_kernel<R, GJ><<<grid, L.W * 32, smem, L.st>>>(*L.a);
-        return cudaGetLastError();
+        return launch_k(dense_step_kernel<R, GJ>, dim3(grid), dim3(L.W * 32), smem, L.st, L.a->c.pdl != 0, *L.a);
     }
 };
 

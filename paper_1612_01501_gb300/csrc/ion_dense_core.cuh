@@ -59,11 +59,18 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
             if (__syncthreads_or(!landed)) return false;   // block-uniform decision
         }
         float *tb = sm.tile0 + b * sm.buf_len;
-        for (int j = threadIdx.x; j < len; j += blockDim.x) {
-            const bool real = j0 + j < n;
-            const float u = (tb[j] - m_shift) * GJ_SCALE;
-            tb[j] = real ? -u : -PAD_U;
-            if (real) kahan_add(Us, Uc, u);
+        float4 *tb4w = reinterpret_cast<float4 *>(tb);
+        for (int j4 = threadIdx.x; j4 < (len >> 2); j4 += blockDim.x) {   // four columns per thread and round
+            const float4 v = tb4w[j4];
+            float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const bool real = j0 + 4 * j4 + q < n;
+                const float u = (x[q] - m_shift) * GJ_SCALE;
+                x[q] = real ? -u : -PAD_U;
+                if (real) kahan_add(Us, Uc, u);
+            }
+            tb4w[j4] = make_float4(x[0], x[1], x[2], x[3]);
         }
         __syncthreads();
         const float4 *t4 = reinterpret_cast<const float4 *>(tb);

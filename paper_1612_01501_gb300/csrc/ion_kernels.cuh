@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "ion_async.cuh"
 #include "ion_model.cuh"
 
 namespace ion {
@@ -32,8 +33,28 @@ struct StepCommon {
     uint32_t *status;     // sticky status word
     float *trace;         // V_axon ring [cap][n] or NULL
     int32_t trace_stride, trace_cap;
+    int32_t pdl;          // host side: launch with programmatic stream serialization
     ModelF P;
 };
+
+// Launch a per-step kernel; with `pdl`, with programmatic stream serialization, so that
+// its CTAs may be scheduled while the kernel before it drains (the kernel starts with
+// pdl_enter(), which waits for that kernel's completion before any global access).
+template <class... P, class... A>
+inline cudaError_t launch_k(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl,
+                            A... args) {
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 // V_dend slot holding step t: slot 0 is field F_VDEND, slot 1 is field 19.
 __device__ __forceinline__ float *vd_slot(const StateView &S, int64_t t) {

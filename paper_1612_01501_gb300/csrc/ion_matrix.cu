@@ -27,16 +27,17 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
     const int n = c.n, n_pad = c.n_pad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * 8 * R;
-    const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
-    const DenseSmem sm = dense_smem(smem_raw, n_pad);
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_mbar_init();
     }
+    pdl_enter();
     __syncthreads();
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c, t);
+    float *vnext = vd_next(c, t);
+    const DenseSmem sm = dense_smem(smem_raw, n_pad);
     if (threadIdx.x == 0) {
         issue_tile(sm, vcur, n_pad, 0, bar);
         if (sm.n_tiles > 1) issue_tile(sm, vcur, n_pad, 1, bar);
@@ -162,8 +163,7 @@ int matrix_default_R(int n, int sms) {
 template <int R>
 static cudaError_t matrix_launch_R(const MatrixArgs &a, cudaStream_t st) {
     const int grid = (a.c.n + 8 * R - 1) / (8 * R);
-    matrix_step_kernel<R><<<grid, 256, matrix_smem_bytes(a.c.n_pad), st>>>(a);
-    return cudaGetLastError();
+    return launch_k(matrix_step_kernel<R>, dim3(grid), dim3(256), matrix_smem_bytes(a.c.n_pad), st, a.c.pdl != 0, a);
 }
 cudaError_t launch_matrix_step(const MatrixArgs &a, int R, cudaStream_t st) {
     switch (R) {

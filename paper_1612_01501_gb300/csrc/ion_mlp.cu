@@ -479,6 +479,7 @@ constexpr int SURR_CPW = 16;   // cells per warp
 __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
     __shared__ __align__(16) MlpDev W;
     __shared__ float ys[2][3 * SURR_CPW][MO + 1];
+    pdl_enter();
     const StepCommon &c = a.c;
     load_mlp(W, a.mlp);
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
@@ -777,9 +778,9 @@ static cudaError_t surrogate_step(ion_sim *s, int k_off, const float *iapp) {
     }
     if (e != cudaSuccess) return e;
     SurrArgs sa{c, (const MlpDev *)s->d_mlp, s->kind == ION_NO_GJ ? nullptr : s->d_ic};
-    surrogate_cell_kernel<<<(unsigned)((s->n + 2 * SURR_CPW - 1) / (2 * SURR_CPW)), 64, 0, s->st>>>(sa);
     s->launches++;
-    return cudaGetLastError();
+    return launch_k(surrogate_cell_kernel, dim3((unsigned)((s->n + 2 * SURR_CPW - 1) / (2 * SURR_CPW))), dim3(64), 0,
+                    s->st, c.pdl != 0, sa);
 }
 
 ion_status ion_setup_surrogate(ion_sim *s, const ion_params *p) {

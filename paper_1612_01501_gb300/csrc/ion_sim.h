@@ -71,6 +71,7 @@ struct ion_sim {
     cudaGraphExec_t gexec = nullptr;
     int64_t graph_launches = 0;
     bool no_graph = false;
+    bool pdl_off = false;   // programmatic launches unavailable (graph capture refused them)
     std::string err;
 
     // extension points (persistent, batched and surrogate variants)

@@ -29,6 +29,7 @@ HOST, DEVICE = 0, 1
 FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SPLIT, FLAG_HALF_WORK = 1, 2, 4, 8, 16, 32, 64
 FLAG_CSR_AS_GIVEN = 128
 FLAG_SGJ = 256           # SGJ use case: linear junctions w (V_i - V_j)
+FLAG_NO_PDL = 512        # ordinary launches instead of programmatic dependent launches
 INPUT_NONE, INPUT_PULSES, INPUT_DENSE = 0, 1, 2
 MLP_IN, MLP_HID, MLP_OUT = 2, 64, 24
 

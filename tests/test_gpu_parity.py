@@ -606,3 +606,49 @@ def test_create_destroy_loop_does_not_leak(torch_cuda, O):
     torch.cuda.synchronize()
     free1, _ = torch.cuda.mem_get_info()
     assert free0 - free1 <= 64 << 20, (free0 - free1) / 2**20
+
+
+@pytest.mark.parametrize("case", ["dense", "csr", "csr_staged", "matrix", "no_gj", "sgj_dense", "batch"])
+def test_programmatic_launches_match_ordinary_launches(torch_cuda, case):
+    """Per-step kernels launched with programmatic stream serialization (the default) give
+    the same bits as ordinary launches, over graph replays and direct launches."""
+    n = 6000
+    S0 = ion.ion_default_state(n)
+    S0[0] = (S0[0] + inputs.vdend_jitter(n, 21)).astype(np.float32)
+    g = inputs.junction_weight(0.04, n)
+    if case in ("csr", "csr_staged"):
+        rp, col = inputs.random_symmetric_csr(n, 120, 5)
+        w = np.full(len(col), inputs.junction_weight(0.04, 120), np.float32)
+        tune = dict(csr_staging=2) if case == "csr_staged" else None
+        make = lambda fl: ion.ion_create(n, ion.CSR, row_ptr=rp, col=col, w=w, init_state=S0, flags=fl, tune=tune)
+    elif case == "matrix":
+        W = np.full((n, n), g, np.float32)
+        make = lambda fl: ion.ion_create(n, ion.DENSE_MATRIX, w=W, init_state=S0, flags=fl)
+    elif case == "no_gj":
+        make = lambda fl: ion.ion_create(n, ion.NO_GJ, init_state=S0, flags=fl)
+    elif case == "sgj_dense":
+        make = lambda fl: ion.ion_create(n, ion.DENSE_UNIFORM, g=g, init_state=S0, flags=fl | ion.FLAG_SGJ)
+    elif case == "batch":
+        rp, col = inputs.random_symmetric_csr(3000, 20, 6)
+        nets = [dict(n=3000, kind=ion.DENSE_UNIFORM, g=inputs.junction_weight(0.04, 3000)),
+                dict(n=3000, kind=ion.CSR, row_ptr=rp, col=col, w=np.full(len(col), 2e-3, np.float32))]
+        make = lambda fl: ion.ion_create_batch(nets, init_state=S0, flags=fl)
+    else:
+        make = lambda fl: ion.ion_create(n, ion.DENSE_UNIFORM, g=g, init_state=S0, flags=fl)
+    pul = (np.array([0, 17, 4000], np.int32), np.array([2, 5, 40], np.int64), np.array([30, 60, 90], np.int64),
+           np.array([6.0, 4.0, 5.0], np.float32))
+    out = []
+    for extra in (0, ion.FLAG_NO_PDL):
+        h = make(ion.FLAG_KAHAN | extra)
+        try:
+            ion.ion_set_input(h, pul)
+            ion.ion_set_trace(h, 1, 130)
+            ion.ion_step(h, 100)        # graph replays
+            ion.ion_step(h, 27)         # direct launches
+            ion.ion_sync(h)
+            out.append((ion.ion_read_state(h, n), ion.ion_read_trace(h, n, 127)))
+        finally:
+            ion.ion_destroy(h)
+    assert np.isfinite(out[0][0]).all()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
