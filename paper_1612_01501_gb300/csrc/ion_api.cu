@@ -337,8 +337,7 @@ ion_status ion_prepare_csr_chunk(ion_sim *s) {
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 void ion_sim_free_device(ion_sim *s) {
-    if (s->gexec) cudaGraphExecDestroy(s->gexec);
-    s->gexec = nullptr;
+    ion_drop_graphs(s);
     cudaFree(s->d_state);
     cudaFree(s->d_t);
     cudaFree(s->d_status);
@@ -627,10 +626,7 @@ static ion_status install_pulses(ion_sim *s, const ion_input *in) {
     s->d_pbeg = s->d_pend = nullptr;
     s->d_pamp = nullptr;
     s->n_pulses = 0;
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    ion_drop_graphs(s);
     if (np == 0) return ION_OK;
     cudaError_t e = ion_alloc(&s->d_poff, (s->n + 1) * sizeof(int32_t));
     if (e == cudaSuccess) e = ion_alloc(&s->d_pbeg, np * sizeof(int64_t));
@@ -676,6 +672,7 @@ StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp) {
     c.n_pad = s->n_pad;
     c.t_dev = s->d_t;
     c.k_off = k_off;
+    c.par = (int32_t)((s->t_enq + k_off) & 1);
     c.vd_fixed = 0;
     c.pulses.off = s->n_pulses > 0 ? s->d_poff : nullptr;   // no table unless one is complete
     c.pulses.begin = s->d_pbeg;
@@ -774,6 +771,7 @@ static cudaError_t enqueue_steps_direct(ion_sim *s, int64_t k, const float *iapp
         cudaError_t e = launch_advance(s->d_t, chunk, s->st);
         s->launches++;
         if (e != cudaSuccess) return e;
+        s->t_enq += chunk;
         done += chunk;
     }
     return cudaSuccess;
@@ -793,10 +791,11 @@ static ion_status build_graph_once(ion_sim *s) {
         if (g) cudaGraphDestroy(g);
         return ion_fail(s, ION_ERR_CUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&s->gexec, g, 0);
+    cudaGraphExec_t &gx = s->gexec[s->t_enq & 1];   // its launches take the parity of the current step
+    e = cudaGraphInstantiate(&gx, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        s->gexec = nullptr;
+        gx = nullptr;
         return ion_fail(s, ION_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
     }
     s->graph_launches = (int64_t)K * s->launches_per_step() + 1;   // + the counter advance
@@ -861,17 +860,18 @@ extern "C" ion_status ion_step(ion_sim *s, int64_t n_steps, const ion_input *inp
         return ION_OK;
     }
     int64_t left = n_steps;
+    s->t_enq = s->t;
     const bool graphs = !(s->flags & ION_FLAG_NO_GRAPH) && iapp == nullptr && !s->no_graph;
-    if (graphs && left >= s->graph_steps) {
-        if (!s->gexec) {
+    while (graphs && left >= s->graph_steps) {
+        const int p = (int)(s->t_enq & 1);
+        if (!s->gexec[p]) {
             ion_status st = build_graph(s);
             if (st != ION_OK) return st;
         }
-        while (left >= s->graph_steps) {
-            ION_CK(s, cudaGraphLaunch(s->gexec, s->st));
-            s->launches += s->graph_launches;
-            left -= s->graph_steps;
-        }
+        ION_CK(s, cudaGraphLaunch(s->gexec[p], s->st));
+        s->launches += s->graph_launches;
+        left -= s->graph_steps;
+        s->t_enq += s->graph_steps;
     }
     if (left > 0) {
         const float *base = iapp ? iapp + (n_steps - left) * (int64_t)s->n : nullptr;
@@ -891,6 +891,8 @@ extern "C" ion_status ion_sync(ion_sim *s) {
     s->sticky |= st;
     if (s->sticky & ST_TIMEOUT) return ion_fail(s, ION_ERR_TIMEOUT, "a bounded device wait timed out");
     if (s->sticky & ST_NONFINITE) return ion_fail(s, ION_ERR_NONFINITE, "non-finite voltage or [Ca] in the state");
+    if (s->sticky & ST_SLOT)
+        return ion_fail(s, ION_ERR_CUDA, "the device step counter and the host's step count disagree");
     return ION_OK;
 }
 
@@ -990,10 +992,7 @@ extern "C" ion_status ion_set_trace(ion_sim *s, int32_t stride, int32_t capacity
     s->d_trace = nullptr;
     s->trace_stride = 0;
     s->trace_cap = 0;
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    ion_drop_graphs(s);
     if (stride == 0 || capacity == 0) return ION_OK;
     ION_CK(s, ion_alloc(&s->d_trace, (size_t)capacity * s->n * sizeof(float)));
     s->trace_stride = stride;

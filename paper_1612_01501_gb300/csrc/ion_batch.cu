@@ -130,8 +130,8 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
     const BatchTile T = a.tiles[blockIdx.x];
     const StepCommon &c = a.c;
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (T.kind == TILE_DENSE) {
@@ -296,10 +296,7 @@ static ion_status batch_plan(ion_sim *s) {
     std::vector<BatchTile> sorted(tiles.size());
     for (size_t k = 0; k < order.size(); ++k) sorted[k] = tiles[order[k]];
     cudaError_t e = cudaStreamSynchronize(s->st);
-    if (s->gexec) {   // the captured steps hold the old tile list
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    ion_drop_graphs(s);   // the captured steps hold the old tile list
     if (e == cudaSuccess && X->d_tiles) e = cudaFree(X->d_tiles);
     X->d_tiles = nullptr;   // until a new list is in place, stepping is refused
     X->n_tiles = 0;
@@ -754,10 +751,7 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
         bt.csr_rows_per_cta = bstaged ? s->csr_chunk_rows : brows;
         bt.csr_staging = bstaged ? 2 : 1;
     }
-    if (s->gexec) {
-        cudaGraphExecDestroy(s->gexec);
-        s->gexec = nullptr;
-    }
+    ion_drop_graphs(s);
     cudaFree(save);
     if (st != ION_OK) return st;
     if (chosen) *chosen = bt;

@@ -30,8 +30,8 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     const int n = c.n;
     const int row0 = blockIdx.x * rows;
     const int64_t t = step_index(c);
-    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
-    float *vnext = a.fuse ? vd_next(c, t) : nullptr;
+    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c);
+    float *vnext = a.fuse ? vd_next(c) : nullptr;
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (rows + nsub - 1) / nsub;          // the same for every lane (shuffles below)
     for (int it = 0; it < iters; ++it) {
@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
     const int n = c.n;
     const int row0 = blockIdx.x * rows;
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (rows + nsub - 1) / nsub;
     if (threadIdx.x == 0) {
@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(256) sgj_partial_kernel(const StepCommon c, fl
     __shared__ float red[8];
     pdl_enter();
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
+    const float *vcur = vd_cur(c);
     const float m = vcur[0];
     float s = 0.0f, cc = 0.0f;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < c.n; j += (int64_t)gridDim.x * blockDim.x)
@@ -303,8 +303,8 @@ __global__ void __launch_bounds__(256) sgj_dense_update_kernel(const StepCommon 
     __shared__ float red[8];
     pdl_enter();
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     if (part == nullptr) {
         const float m0 = vcur[0];
         float s = 0.0f, cc = 0.0f;
@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(256) sgj_csr_step_kernel(const CsrArgs a) {
     pdl_enter();
     const StepCommon &c = a.c;
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     const int sub = threadIdx.x >> 3, li = threadIdx.x & 7;
     const int i = blockIdx.x * 32 + sub;
     float acc = 0.0f;
@@ -401,8 +401,8 @@ __global__ void __launch_bounds__(256) cell_step_kernel(const CellArgs a) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= c.n) return;
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     const Cell cell = load_cell(c.S, vcur, i);
     const float ic = a.ic != nullptr ? a.ic[i] : 0.0f;
     float iapp = pulse_current(c.pulses, i, t);

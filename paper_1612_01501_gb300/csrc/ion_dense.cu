@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     pdl_enter();
 
     const int64_t t = step_index(c);
-    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c, t);
-    float *vnext = a.fuse ? vd_next(c, t) : nullptr;
+    const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c);
+    float *vnext = a.fuse ? vd_next(c) : nullptr;
     const int row_base = blockIdx.x * rows_cta;
     __syncthreads();
     if (threadIdx.x == 0)

@@ -19,6 +19,7 @@ static ion_status half_run(ion_sim *s, int64_t n_steps, const float *iapp) {
         const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 22);   // 2 * chunk * grid < 2^32
         HalfArgs a{};
         a.c = ion_step_common(s, 0, nullptr);
+        a.c.par = -1;   // many steps per launch: the slots follow the device counter
         a.g = s->g;
         a.n_steps = chunk;
         a.rows = (s->persist_W / s->persist_GJ) * s->persist_R;
@@ -48,6 +49,7 @@ static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
         const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 24);
         PersistArgs a{};
         a.c = ion_step_common(s, 0, nullptr);
+        a.c.par = -1;   // many steps per launch: the slots follow the device counter
         a.g = s->g;
         a.n_steps = chunk;
         a.kahan = 1;

@@ -27,6 +27,9 @@ struct StepCommon {
     int32_t n_pad;        // V_dend length incl. sentinel padding (multiple of PAD_J)
     const int64_t *t_dev; // absolute index of the first step of the current replay (NULL: t = 0)
     int32_t k_off;        // this launch's step offset from *t_dev
+    int32_t par;          // parity of this launch's step index t (the V_dend slot of step t),
+                          // passed by the host so that the slot address does not wait on *t_dev;
+                          // -1 in persistent launches (which run many steps)
     int32_t vd_fixed;     // 1: V_dend is updated in place in slot 0 (single-cell-launch primitives)
     PulseTable pulses;
     const float *iapp;    // dense evoked input of this step (n floats) or NULL
@@ -63,11 +66,11 @@ __device__ __forceinline__ float *vd_slot(const StateView &S, int64_t t) {
 __device__ __forceinline__ int64_t step_index(const StepCommon &c) {
     return c.t_dev != nullptr ? *c.t_dev + c.k_off : (int64_t)c.k_off;
 }
-__device__ __forceinline__ float *vd_cur(const StepCommon &c, int64_t t) {
-    return c.vd_fixed ? c.S.base : vd_slot(c.S, t);
+__device__ __forceinline__ float *vd_cur(const StepCommon &c) {
+    return c.vd_fixed ? c.S.base : vd_slot(c.S, c.par);
 }
-__device__ __forceinline__ float *vd_next(const StepCommon &c, int64_t t) {
-    return c.vd_fixed ? c.S.base : vd_slot(c.S, t + 1);
+__device__ __forceinline__ float *vd_next(const StepCommon &c) {
+    return c.vd_fixed ? c.S.base : vd_slot(c.S, c.par + 1);
 }
 
 // Write the step result of cell i (and its trace sample, status bit).
@@ -75,6 +78,7 @@ __device__ __forceinline__ void finish_cell(const StepCommon &a, int64_t t, floa
                                             const CellNext &o) {
     store_cell(a.S, vd_next, i, o);
     if (!cell_finite(o)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
+    if (a.par >= 0 && (int)(t & 1) != a.par) atomicOr(a.status, (uint32_t)ST_SLOT);   // host and device disagree
     if (a.trace != nullptr && ((t + 1) % a.trace_stride) == 0) {
         const int64_t sample = (t + 1) / a.trace_stride - 1;
         a.trace[(sample % a.trace_cap) * (int64_t)a.n + i] = o.va;

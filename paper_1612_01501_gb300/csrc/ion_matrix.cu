@@ -35,8 +35,8 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
     pdl_enter();
     __syncthreads();
     const int64_t t = step_index(c);
-    const float *vcur = vd_cur(c, t);
-    float *vnext = vd_next(c, t);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     const DenseSmem sm = dense_smem(smem_raw, n_pad);
     if (threadIdx.x == 0) {
         issue_tile(sm, vcur, n_pad, 0, bar);

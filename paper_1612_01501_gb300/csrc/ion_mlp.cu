@@ -485,8 +485,8 @@ __global__ void __launch_bounds__(64) surrogate_cell_kernel(const SurrArgs a) {
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
     const int64_t base = ((int64_t)blockIdx.x * 2 + warp) * SURR_CPW;
     const int64_t tstep = step_index(c);
-    const float *vcur = vd_cur(c, tstep);
-    float *vnext = vd_next(c, tstep);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
     __syncthreads();
 #pragma unroll 1
     for (int mt = 0; mt < 3; ++mt) {

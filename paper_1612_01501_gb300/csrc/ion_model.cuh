@@ -271,16 +271,18 @@ struct PulseTable {
     const int64_t *end;
     const float *amp;
 };
-__device__ __forceinline__ float pulse_current(const PulseTable &T, int64_t i, int64_t t) {
-    if (T.off == nullptr) return 0.0f;
+__device__ __forceinline__ float pulse_current_range(const PulseTable &T, int32_t p0, int32_t p1, int64_t t) {
     float I = 0.0f;
-    const int32_t p0 = T.off[i], p1 = T.off[i + 1];
     for (int32_t p = p0; p < p1; ++p)
         if (t >= T.begin[p] && t < T.end[p]) I += T.amp[p];
     return I;
 }
+__device__ __forceinline__ float pulse_current(const PulseTable &T, int64_t i, int64_t t) {
+    if (T.off == nullptr) return 0.0f;
+    return pulse_current_range(T, T.off[i], T.off[i + 1], t);
+}
 
 // Status word bits set by kernels (sticky until read by the host).
-enum StatusBits : uint32_t { ST_NONFINITE = 1u, ST_TIMEOUT = 2u };
+enum StatusBits : uint32_t { ST_NONFINITE = 1u, ST_TIMEOUT = 2u, ST_SLOT = 4u };
 
 }  // namespace ion

@@ -68,7 +68,8 @@ struct ion_sim {
     int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
     int32_t *d_mid = nullptr;       // interior chunk boundaries per row
     void *d_mlp = nullptr;          // packed surrogate weights (ION_FLAG_SURROGATE)
-    cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // K-step graphs, by the parity of their first step
+    int64_t t_enq = 0;              // the device step counter's value where the next launch is enqueued
     int64_t graph_launches = 0;
     bool no_graph = false;
     bool pdl_off = false;   // programmatic launches unavailable (graph capture refused them)
@@ -107,6 +108,13 @@ void ion_choose_dense_shape(int n, int sms, int *R, int *W, int *GJ);
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
 ion_status ion_setup_csr_staging(ion_sim *s, int mode);
 void ion_sim_free_device(ion_sim *s);
+// destroy the captured step graphs (after any change they depend on)
+inline void ion_drop_graphs(ion_sim *s) {
+    for (cudaGraphExec_t &g : s->gexec) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
+}
 // per-flag setup of the extensions (ion_ext.cu)
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p);
 // batch state I/O in the user's numbering (ion_batch.cu)
