@@ -49,10 +49,7 @@ K3_SWEEP = (1 << 16, 1 << 18, 1 << 20, 1 << 22)
 # DRAM bytes (read + write) per launch of the line's dominant kernel, from one ncu capture
 # of that kernel in its current form (the summaries under profiles/ give the commands);
 # None where no capture matches the line's kernel and shape
-TRAFFIC = {
-    ("c2", "dense_step_kernel"): (519.2e3, "profiles/dense_step_kernel_c2_8192.md"),
-    ("c3_k1000", "csr_chunk_step_kernel"): (139.5e6, "profiles/csr_chunk_step_kernel_c3_k1000_compact.md"),
-    ("k3", "cell_step_kernel"): (517.0e6, "profiles/cell_step_kernel_k3_4194304.md"),
+TRAFFIC = {   # (bytes per launch, source); an entry is removed when its kernel changes until re-captured
 }
 
 

@@ -60,6 +60,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Ask for [src, src + bytes) to be brought into L2, without completion tracking (a hint).
+// src 16-byte aligned, bytes a multiple of 16, the range inside one allocation.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     const float y = x - comp;
     const float t = sum + y;

@@ -66,13 +66,24 @@ __device__ __forceinline__ void batch_csr_rows16(const BatchArgs &a, const Batch
                                                  float *ic_s) {
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (T.rows + nsub - 1) / nsub;
+    int e0n = 0, e1n = 0;   // the next row's bounds and V_dend, loaded one row ahead
+    float vin = 0.0f;
+    if (sub < T.rows) {
+        e0n = a.row_ptr[T.row0 + sub];
+        e1n = a.row_ptr[T.row0 + sub + 1];
+        vin = vcur[T.row0 + sub];
+    }
     for (int it = 0; it < iters; ++it) {
         const int rr = sub + it * nsub;
-        float acc = 0.0f;
-        if (rr < T.rows) {
-            const int i = T.row0 + rr;
-            acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li, vj);
+        const int e0 = e0n, e1 = e1n;
+        const float vi = vin;
+        if (rr + nsub < T.rows) {
+            e0n = a.row_ptr[T.row0 + rr + nsub];
+            e1n = a.row_ptr[T.row0 + rr + nsub + 1];
+            vin = vcur[T.row0 + rr + nsub];
         }
+        float acc = 0.0f;
+        if (rr < T.rows) acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, e0, e1, vi, li, vj);
 #pragma unroll
         for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (li == 0 && rr < T.rows) ic_s[rr] = (HAS_W ? acc : acc * T.g) * (1.0f / GJ_SCALE);
@@ -102,15 +113,26 @@ __device__ __forceinline__ void batch_csr_rows(const BatchArgs &a, const BatchTi
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (T.rows + nsub - 1) / nsub;
     const bool vec = ((uintptr_t)a.col % 16 == 0) && ((uintptr_t)a.w % 16 == 0);
+    int e0n = 0, e1n = 0;   // the next row's bounds and V_dend, loaded one row ahead
+    float vin = 0.0f;
+    if (sub < T.rows) {
+        e0n = a.row_ptr[T.row0 + sub];
+        e1n = a.row_ptr[T.row0 + sub + 1];
+        vin = vcur[T.row0 + sub];
+    }
     for (int it = 0; it < iters; ++it) {
         const int rr = sub + it * nsub;
-        float acc = 0.0f;
-        if (rr < T.rows) {
-            const int i = T.row0 + rr;
-            const int e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
-            acc = vec ? csr_row_sum<SW, true, true>(vcur, a.col, a.w, e0, e1, vcur[i], li)
-                      : csr_row_sum<SW, false, true>(vcur, a.col, a.w, e0, e1, vcur[i], li);
+        const int e0 = e0n, e1 = e1n;
+        const float vi = vin;
+        if (rr + nsub < T.rows) {
+            e0n = a.row_ptr[T.row0 + rr + nsub];
+            e1n = a.row_ptr[T.row0 + rr + nsub + 1];
+            vin = vcur[T.row0 + rr + nsub];
         }
+        float acc = 0.0f;
+        if (rr < T.rows)
+            acc = vec ? csr_row_sum<SW, true, true>(vcur, a.col, a.w, e0, e1, vi, li)
+                      : csr_row_sum<SW, false, true>(vcur, a.col, a.w, e0, e1, vi, li);
 #pragma unroll
         for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
         if (li == 0 && rr < T.rows) ic_s[rr] = acc * (1.0f / GJ_SCALE);

@@ -34,16 +34,31 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     float *vnext = a.fuse ? vd_next(c) : nullptr;
     const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
     const int iters = (rows + nsub - 1) / nsub;          // the same for every lane (shuffles below)
+    // a row's bounds and V_dend are loaded one row ahead (see the chunked variant)
+    auto bounds = [&](int it, int &e0, int &e1, float &vi) {
+        const int rr = sub + it * nsub, i = row0 + rr;
+        e0 = e1 = 0;
+        vi = 0.0f;
+        if (it < iters && rr < rows && i < n) {
+            e0 = a.row_ptr[i];
+            e1 = a.row_ptr[i + 1];
+            vi = vcur[i];
+        }
+    };
+    int e0n, e1n;
+    float vin;
+    bounds(0, e0n, e1n, vin);
     for (int it = 0; it < iters; ++it) {
         const int rr = sub + it * nsub;
-        const int i = row0 + rr;
+        const int e0 = e0n, e1 = e1n;
+        const float vi = vin;
+        bounds(it + 1, e0n, e1n, vin);
         float acc = 0.0f;
-        if (rr < rows && i < n) {
+        if (e1 > e0) {   // rows past the end (and empty rows) have e0 == e1
             if (C16)
-                acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li,
-                                                      VjGlobal{vcur});
+                acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, e0, e1, vi, li, VjGlobal{vcur});
             else
-                acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, a.row_ptr[i], a.row_ptr[i + 1], vcur[i], li);
+                acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, e0, e1, vi, li);
         }
 #pragma unroll
         for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
@@ -158,18 +173,62 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             }
             return;
         }
+        // The bounds of a row's segment in this chunk and its V_dend.  With 16 or more lanes
+        // per row (long rows, few rows per group) they are loaded two rows ahead and the
+        // next row's index (and weight) stream is requested into L2 one row ahead, so that
+        // each row waits on an L2 latency rather than on two HBM latencies.
+        auto bounds = [&](int it, int &e0, int &e1, float &vi) {
+            const int rr = sub + it * nsub, i = row0 + rr;
+            e0 = e1 = 0;
+            vi = 0.0f;
+            if (it < iters && rr < rows && i < n) {
+                e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
+                e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+                vi = vcur[i];
+            }
+        };
+        constexpr bool AHEAD = SW >= 16;
+        int e0n = 0, e1n = 0, e0m = 0, e1m = 0;
+        float vin = 0.0f, vim = 0.0f;
+        if (AHEAD) {
+            bounds(0, e0n, e1n, vin);
+            bounds(1, e0m, e1m, vim);
+        }
         for (int it = 0; it < iters; ++it) {
             const int rr = sub + it * nsub;
-            const int i = row0 + rr;
+            int e0, e1;
+            float vi;
+            if (AHEAD) {
+                e0 = e0n;
+                e1 = e1n;
+                vi = vin;
+                e0n = e0m;
+                e1n = e1m;
+                vin = vim;
+                bounds(it + 2, e0m, e1m, vim);
+                if (li == 0 && e1n > e0n) {   // the next row's stream, in whole 16-byte groups
+                    if (C16) {   // col16 is padded to whole 16-byte groups
+                        const int64_t b0 = ((int64_t)e0n * 2) & ~(int64_t)15, b1 = ((int64_t)e1n * 2 + 15) & ~(int64_t)15;
+                        bulk_prefetch_l2(reinterpret_cast<const char *>(a.col16) + b0, (uint32_t)(b1 - b0));
+                    } else {     // 32-bit columns: the last partial group is left out
+                        const int64_t b0 = ((int64_t)e0n * 4) & ~(int64_t)15, b1 = ((int64_t)e1n * 4) & ~(int64_t)15;
+                        if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const char *>(a.col) + b0, (uint32_t)(b1 - b0));
+                    }
+                    if (HAS_W) {
+                        const int64_t b0 = ((int64_t)e0n * 4) & ~(int64_t)15, b1 = ((int64_t)e1n * 4) & ~(int64_t)15;
+                        if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const char *>(a.w) + b0, (uint32_t)(b1 - b0));
+                    }
+                }
+            } else {
+                bounds(it, e0, e1, vi);
+            }
             float acc = 0.0f;
-            if (rr < rows && i < n) {
-                const int e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
-                const int e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+            if (e1 > e0) {   // rows past the end (and empty segments) have e0 == e1
                 if (C16)
-                    acc = csr_row_sum16<SW, HAS_W, true>(a.col16, a.w, e0, e1, vcur[i], li,
+                    acc = csr_row_sum16<SW, HAS_W, true>(a.col16, a.w, e0, e1, vi, li,
                                                          VjChunk{vs, (uint32_t)c0 & 0xFFFFu});
                 else
-                    acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vcur[i], li);
+                    acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vi, li);
             }
 #pragma unroll
             for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);

@@ -27,6 +27,13 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
     const int n = c.n, n_pad = c.n_pad;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = blockIdx.x * 8 * R;
+    constexpr int BLK = 8;   // float4 groups per lane between Kahan folds: a block is 32 * BLK groups (4 KB) per row
+    const float *wrow[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) wrow[r] = a.W + (int64_t)min(row0 + warp * R + r, n - 1) * n_pad;   // rows past n: any row
+    if (lane == 0)   // the weights are constant: their first two blocks are requested into L2 before the wait
+#pragma unroll
+        for (int r = 0; r < R; ++r) bulk_prefetch_l2(wrow[r], (uint32_t)min(2 * 32 * BLK * 16, n_pad * 4));
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -44,12 +51,10 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
     }
     const float m_shift = vcur[0];
     float ui[R];
-    const float *wrow[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = row0 + warp * R + r;
         ui[r] = row < n ? (vcur[row] - m_shift) * GJ_SCALE : 0.0f;
-        wrow[r] = a.W + (int64_t)min(row, n - 1) * n_pad;   // rows past n: any row, result unused
     }
     float ks[R], kc[R];
 #pragma unroll
@@ -78,8 +83,12 @@ __global__ void __launch_bounds__(256) matrix_step_kernel(const MatrixArgs a) {
         __syncthreads();
         const float4 *t4 = reinterpret_cast<const float4 *>(tb);
         const int n4 = len >> 2;
-        constexpr int BLK = 8;            // float4 groups per lane between Kahan folds
         for (int m0 = lane; m0 < n4; m0 += 32 * BLK) {
+            const int nb = m0 - lane + 2 * 32 * BLK;   // the block after next, requested into L2 now
+            if (lane == 0 && nb < n4)
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    bulk_prefetch_l2(wrow[r] + j0 + 4 * nb, (uint32_t)min(32 * BLK, n4 - nb) * 16u);
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
