@@ -92,3 +92,30 @@ def test_malformed_csr_rejected(L):
     rp4 = rp.copy()
     rp4[-1] -= 1
     assert _create_err(n=n, kind=ion.CSR, row_ptr=rp4, col=col[:-1].copy()) in (ion.ERR_BAD_CSR,)
+
+
+def _header_constants():
+    """Explicitly valued enumerators of include/ion.h (name -> int)."""
+    txt = open(os.path.join(ROOT, "include", "ion.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for name, expr in re.findall(r"\b(ION_[A-Z0-9_]+)\s*=\s*(-?[0-9]+u?(?:\s*<<\s*[0-9]+)?)", txt):
+        out[name] = eval(expr.replace("u", ""))
+    return out
+
+
+def test_binding_constants_match_header():
+    """The Python names of every status, kind, flag, memory and input constant carry the
+    header's values (a drift here would pass wrong flags through the ABI)."""
+    h = _header_constants()
+    pairs = {"ION_OK": ion.OK, "ION_FIELD_ALL": ion.FIELD_ALL, "ION_HOST": ion.HOST, "ION_DEVICE": ion.DEVICE}
+    for name in h:
+        for prefix in ("ION_ERR_", "ION_FLAG_", "ION_INPUT_"):
+            if name.startswith(prefix):
+                pairs[name] = getattr(ion, name[len("ION_"):])
+    for kind in ("DENSE_UNIFORM", "CSR", "NO_GJ", "DENSE_MATRIX"):
+        pairs["ION_" + kind] = getattr(ion, kind)
+    assert len(pairs) >= 25
+    for name, val in pairs.items():
+        assert h[name] == val, (name, h[name], val)
+    assert ion.STATUS_NAMES[ion.ERR_OOM] == "OOM"
