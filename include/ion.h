@@ -186,6 +186,9 @@ typedef struct {
     int32_t csr_staging;         /* single CSR networks: 0 = choose, 1 = gather V_dend
                                     through L1/L2, 2 = stage V_dend in shared memory
                                     128 KB at a time (one CTA per SM)                */
+    int32_t csr_bank_order;      /* single CSR networks with equal weights: 1 = store the
+                                    16-bit columns in shared-memory bank order (see
+                                    ion_csr_bank_order); 0 = as sorted.  Read at creation */
 } ion_tune;
 
 typedef struct ion_sim ion_sim;
@@ -285,6 +288,19 @@ ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
  * ION_FLAG_CSR_AS_GIVEN turns them off.  Dense / NGJ handles report 0, 0, 0.  Any output
  * pointer may be NULL. */
 ion_status ion_csr_layout(const ion_sim *sim, int32_t *index_bytes, int32_t *weight_bytes, int32_t *staged);
+
+/* Edge order for the shared-memory gathers of the staged CSR kernel (host only, no device
+ * call).  The kernel reads the 16-byte-aligned body of each row's per-chunk segment
+ * (columns in [c chunk, (c + 1) chunk)) as groups of eight edges, lane l of a row taking
+ * groups l, l + lanes, ...; one gather reads position k of one round of groups, and its
+ * shared-memory banks are the columns mod 32.  perm[e] (nnz = row_ptr[n] entries, caller
+ * owned) receives the original index of the edge to place at position e: a permutation
+ * within each segment's body that gives every gather set distinct banks where the row
+ * allows it (heads and tails keep their order).  col_idx must be ascending per row;
+ * chunk a positive multiple of 32; lanes_per_row 8, 16 or 32.  Errors: INVALID_ARG,
+ * BAD_CSR (row_ptr not monotone from 0, or a row not ascending). */
+ion_status ion_csr_bank_order(int32_t n, const int32_t *row_ptr, const int32_t *col_idx, int32_t chunk,
+                              int32_t lanes_per_row, int32_t *perm);
 
 /* Test hook, never called in production: the device allocation that follows the next
  * `after` ones (in any handle of the process) reports out-of-memory, once, so that the

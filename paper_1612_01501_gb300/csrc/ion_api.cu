@@ -532,7 +532,15 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
                 e = cudaMemcpyAsync(s->d_col, conn->col_idx, (size_t)s->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
             if (e == cudaSuccess && s->d_w)
                 e = cudaMemcpyAsync(s->d_w, conn->weight, (size_t)s->nnz * sizeof(float), cudaMemcpyHostToDevice, s->st);
-            if (e == cudaSuccess && s->d_col16) e = launch_csr_col16(s->d_col, s->nnz, round_up(s->nnz, 8), s->d_col16, s->st);
+            if (e == cudaSuccess && s->d_col16) {
+                const ion_tune *tb = (const ion_tune *)params->tune;
+                std::vector<uint16_t> h16;   // opt-in: bank order (uniform weights only: no weight array to permute)
+                if (tb && tb->csr_bank_order == 1 && !keep_w &&
+                    ion_csr_bank_col16(s->n, s->n_pad, conn->row_ptr, conn->col_idx, h16))
+                    e = cudaMemcpy(s->d_col16, h16.data(), h16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
+                else
+                    e = launch_csr_col16(s->d_col, s->nnz, round_up(s->nnz, 8), s->d_col16, s->st);
+            }
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: CSR copy: %s", cudaGetErrorString(e)));
         }
         int SW, rows;

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "ion.h"
 #include "ion_kernels.cuh"
@@ -106,6 +107,9 @@ float *ion_field_ptr(ion_sim *s, int32_t field);
 ion_status ion_validate_csr(int32_t n, const ion_conn *c);
 void ion_choose_dense_shape(int n, int sms, int *R, int *W, int *GJ);
 void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
+// 16-bit columns of a sorted host CSR in shared-memory bank order (ion_bank.cu)
+bool ion_csr_bank_col16(int32_t n, int32_t n_pad, const int32_t *row_ptr, const int32_t *col,
+                        std::vector<uint16_t> &out);
 ion_status ion_setup_csr_staging(ion_sim *s, int mode);
 void ion_sim_free_device(ion_sim *s);
 // destroy the captured step graphs (after any change they depend on)

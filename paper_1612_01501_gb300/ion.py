@@ -74,7 +74,7 @@ class ion_tune(ctypes.Structure):
     _fields_ = [("dense_rows_per_warp", ctypes.c_int32), ("dense_warps", ctypes.c_int32),
                 ("dense_col_splits", ctypes.c_int32), ("csr_lanes_per_row", ctypes.c_int32),
                 ("csr_rows_per_cta", ctypes.c_int32), ("csr_lanes_scale", ctypes.c_int32),
-                ("csr_staging", ctypes.c_int32)]
+                ("csr_staging", ctypes.c_int32), ("csr_bank_order", ctypes.c_int32)]
 
 
 class ion_surrogate_weights(ctypes.Structure):
@@ -112,6 +112,8 @@ _SIGS = {
     "ion_trace_wait": (ctypes.c_int, [ctypes.c_void_p]),
     "ion_step_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "ion_debug_fail_alloc": (ctypes.c_int, [ctypes.c_int32]),
+    "ion_csr_bank_order": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_void_p]),
     "ion_csr_layout": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     "ion_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ion_tune)]),
@@ -391,6 +393,16 @@ def ion_csr_layout(h) -> dict:
     ib, wb, st = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     _check(lib().ion_csr_layout(h, ctypes.byref(ib), ctypes.byref(wb), ctypes.byref(st)), h)
     return {"index_bytes": ib.value, "weight_bytes": wb.value, "staged": st.value}
+
+
+def ion_csr_bank_order(row_ptr, col, chunk: int, lanes_per_row: int) -> np.ndarray:
+    """Bank-ordered edge permutation of a sorted host CSR (see the header)."""
+    rp = np.ascontiguousarray(row_ptr, np.int32)
+    c = np.ascontiguousarray(col, np.int32)
+    perm = np.zeros(max(1, int(rp[-1])), np.int32)
+    _check(lib().ion_csr_bank_order(len(rp) - 1, rp.ctypes.data, c.ctypes.data, int(chunk), int(lanes_per_row),
+                                    perm.ctypes.data))
+    return perm[:int(rp[-1])]
 
 
 def ion_debug_fail_alloc(after: int):
