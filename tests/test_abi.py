@@ -193,3 +193,11 @@ def test_csr_bank_order_rejects_bad_input(L):
     with pytest.raises(ion.IonError) as ei:
         ion.ion_csr_bank_order(rp, c2, 1024, 8)
     assert ei.value.status == ion.ERR_BAD_CSR
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built library the binding raises; nothing falls back to a CPU path."""
+    monkeypatch.setattr(ion, "LIB_PATH", str(tmp_path / "absent" / "libion.so"))
+    monkeypatch.setattr(ion, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        ion.lib()
