@@ -50,6 +50,28 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+_FLOP_SRC = os.path.join(os.path.dirname(_SRC), "flop_count.cpp")
+_FLOP_EXE = os.path.join(os.path.dirname(_SRC), "flop_count")
+
+
+def build_flop_count(force: bool = False) -> str:
+    """Compile flop_count.cpp: this oracle's source with every double replaced by an
+    operation-counting number type (g++; the oracle's C needs -fpermissive as C++)."""
+    stale = not os.path.exists(_FLOP_EXE) or any(os.path.getmtime(p) > os.path.getmtime(_FLOP_EXE)
+                                                  for p in (_FLOP_SRC, _SRC))
+    if force or stale:
+        tmp = _FLOP_EXE + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O1", "-std=c++17", "-fpermissive", "-w", "-o", tmp, _FLOP_SRC, "-lm"])
+        os.replace(tmp, _FLOP_EXE)
+    return _FLOP_EXE
+
+
+def op_counts() -> dict:
+    """Operation counts of one cell step, one dense gap-junction pair and one SGJ edge."""
+    out = subprocess.check_output([build_flop_count()], text=True)
+    return {k: float(v) for k, v in (line.split() for line in out.splitlines())}
+
+
 def lib():
     global _lib
     with _lock:
