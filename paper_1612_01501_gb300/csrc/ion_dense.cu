@@ -21,6 +21,11 @@
 // butterfly) and across column splits, so results are deterministic.  The fused step
 // then runs the explicit-Euler cell update of the CTA's rows (one thread per row) and
 // writes V_dend(t+1) to the other V_dend buffer.
+//
+// Per-step launches are programmatically dependent (launch_k, pdl_enter): the kernel may
+// be scheduled while the previous step drains, initialises its mbarriers, then waits for
+// that step's completion before its first global access.  The V_dend slot comes from the
+// host-passed parity, so the tile copy is issued without waiting on the step counter.
 #include <cuda_runtime.h>
 
 #include "ion_async.cuh"
