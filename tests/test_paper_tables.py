@@ -13,10 +13,19 @@ def test_state_words(O):
 
 
 def test_conductance_count(O):
-    # 12 maximal conductances + g_int + two area ratios + 5 reversal potentials
-    cond = [p for p in O.PARAMS[:20]]
-    assert len(cond) == GOLD["neuron_conductances"]
-    assert sum(p.startswith("g_") for p in cond) == 13 and sum(p.startswith("V_") for p in cond) == 5
+    """Table "reqs" lists 20 conductances per neuron.  The three-compartment model used here
+    has 13: the 12 maximal channel conductances (4 dendritic, 5 somatic, 3 axonal) and the
+    inter-compartment conductance g_int.  The remaining per-cell constants of the table's
+    first 20 entries are two area ratios (p1, p2) and five reversal potentials, which are
+    not conductances.  The gap to the paper's count is a documented mismatch (the paper
+    prints no equations to resolve it), so this pins the model's own count and the paper's
+    number separately rather than reconciling them."""
+    cond = [p for p in O.PARAMS if p.startswith("g_")]
+    assert cond == ["g_int", "g_CaH", "g_KCa", "g_h", "g_ld", "g_CaL", "g_Na_s", "g_Kdr_s", "g_K_s", "g_ls",
+                    "g_Na_a", "g_K_a", "g_la"]
+    assert len(cond) == 13
+    assert GOLD["neuron_conductances"] == 20             # the paper's figure, not reached by the model
+    assert [p for p in O.PARAMS[:20] if not p.startswith("g_")] == ["p1", "p2", "V_Na", "V_K", "V_Ca", "V_h", "V_L"]
     assert O.PARAMS[20] == "C_m"
 
 
