@@ -68,7 +68,7 @@ int main() {
     S[OF_VDEND] = Flop(-55.0);   // away from rest, so no branch is at its special point
     Flop ic(0.25), iapp(1.0);
     g_count = Counts{};
-    or_cell_step(1, P, Flop(0.05), S, &ic, &iapp, Sn, 1);
+    or_cell_step(1, P, nullptr, Flop(0.05), S, &ic, &iapp, Sn, 1);
     report("cell", g_count, 1.0);
     // one dense pass over 2 cells evaluates 4 ordered pairs (the self pairs included),
     // plus one multiplication by g per row

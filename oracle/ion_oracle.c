@@ -301,8 +301,22 @@ void or_gj_csr_sgj(int n, const int32_t *row_ptr, const int32_t *col, const doub
 
 /* ---- cell update (explicit Euler, all right-hand sides from step t) -------------- */
 
-static void cell_step_one(int n, int i, const double *P, double dt, const double *S,
+/* Per-cell constants (Table "reqs": each neuron has its own conductances).  Pc, when not
+ * NULL, holds OP_NCELL values per cell, structure of arrays (entry p of cell i at
+ * Pc[p * n + i], p in table order 0..19); they replace the table's entries for that cell,
+ * except g_CaL, which is per cell already (state field OF_GCAL). */
+enum { OP_NCELL = 20 };
+
+static void cell_step_one(int n, int i, const double *P_table, const double *Pc, double dt, const double *S,
                           double ic, double iapp, double *Sn) {
+    double P_cell[OP_NPARAMS];
+    const double *P = P_table;
+    if (Pc) {
+        memcpy(P_cell, P_table, sizeof P_cell);
+        for (int p = 0; p < OP_NCELL; ++p)
+            if (p != OP_GCAL) P_cell[p] = Pc[(size_t)p * (size_t)n + (size_t)i];
+        P = P_cell;
+    }
 #define F(f) S[(f) * n + i]
     const double Vd = F(OF_VDEND), Vs = F(OF_VSOMA), Va = F(OF_VAXON), ca = F(OF_CA);
     const double Cm = P[OP_CM];
@@ -367,13 +381,14 @@ static void cell_step_one(int n, int i, const double *P, double dt, const double
 #undef G
 }
 
-/* Advance every cell one step: Sn = S + dt * F(S, ic, iapp).  S and Sn must not alias. */
-void or_cell_step(int n, const double *P, double dt, const double *S, const double *ic,
+/* Advance every cell one step: Sn = S + dt * F(S, ic, iapp).  S and Sn must not alias.
+ * Pc: per-cell constants or NULL (see cell_step_one). */
+void or_cell_step(int n, const double *P, const double *Pc, double dt, const double *S, const double *ic,
                   const double *iapp, double *Sn, int threads) {
 #ifdef _OPENMP
 #pragma omp parallel for schedule(static) num_threads(threads > 0 ? threads : 1)
 #endif
-    for (int i = 0; i < n; ++i) cell_step_one(n, i, P, dt, S, ic ? ic[i] : 0.0, iapp ? iapp[i] : 0.0, Sn);
+    for (int i = 0; i < n; ++i) cell_step_one(n, i, P, Pc, dt, S, ic ? ic[i] : 0.0, iapp ? iapp[i] : 0.0, Sn);
     (void)threads;
 }
 
@@ -387,10 +402,11 @@ void or_cell_step(int n, const double *P, double dt, const double *S, const doub
  *   else the sum of amp[p] over pulses p with cell[p] == i and t_begin[p] <= t < t_end[p].
  * S (19 * n, SoA) holds the step-t0 state on entry and the step-(t0 + n_steps) state on
  * return.  If trace != NULL, trace[(t - t0) * n_trace + c] = V_axon of cell
- * trace_cells[c] after step t.  Returns 0, or -1 if scratch could not be allocated.
+ * trace_cells[c] after step t.  Pc: per-cell constants or NULL (see cell_step_one).
+ * Returns 0, or -1 if scratch could not be allocated.
  */
 int or_run(int n, int kind, double g, const int32_t *row_ptr, const int32_t *col,
-           const double *w, const double *P, double dt, double *S, int64_t t0,
+           const double *w, const double *P, const double *Pc, double dt, double *S, int64_t t0,
            int64_t n_steps, const float *iapp_dense, int n_pulses, const int32_t *p_cell,
            const int64_t *p_begin, const int64_t *p_end, const double *p_amp,
            int n_trace, const int32_t *trace_cells, double *trace, int threads) {
@@ -418,7 +434,7 @@ int or_run(int n, int kind, double g, const int32_t *row_ptr, const int32_t *col
             for (int p = 0; p < n_pulses; ++p)
                 if (t >= p_begin[p] && t < p_end[p]) iapp[p_cell[p]] += p_amp[p];
         }
-        or_cell_step(n, P, dt, S, ic, iapp, Sn, threads);
+        or_cell_step(n, P, Pc, dt, S, ic, iapp, Sn, threads);
         memcpy(S, Sn, sizeof(double) * (size_t)OF_NFIELDS * (size_t)n);
         if (trace)
             for (int c = 0; c < n_trace; ++c)

@@ -35,6 +35,7 @@ PARAMS = ("g_int", "p1", "p2", "g_CaH", "g_KCa", "g_h", "g_ld", "g_CaL", "g_Na_s
           "g_Kdr_s", "g_K_s", "g_ls", "g_Na_a", "g_K_a", "g_la", "V_Na", "V_K", "V_Ca",
           "V_h", "V_L", "C_m", "ca_in", "ca_out", "V_0", "Ca_0")
 P = {name: i for i, name in enumerate(PARAMS)}
+NCELLPARAMS = 20   # per-cell constants: table entries 0..19 (g_CaL's row unused)
 
 DENSE, CSR, NOGJ, DENSE_SGJ, CSR_SGJ, MATRIX = 0, 1, 2, 3, 4, 5   # SGJ: linear junctions (Sec. 2.3.2)
 DT_MS = 0.05  # Sec. 2.2: delta = 50 us
@@ -94,9 +95,9 @@ def lib():
             L.or_gj_dense_sgj.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, ctypes.c_int]
             L.or_gj_matrix.argtypes = [ctypes.c_int, dp, dp, dp, ctypes.c_int]
             L.or_gj_csr_sgj.argtypes = [ctypes.c_int, ip, ip, dp, dp, dp, ctypes.c_int]
-            L.or_cell_step.argtypes = [ctypes.c_int, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
+            L.or_cell_step.argtypes = [ctypes.c_int, dp, dp, ctypes.c_double, dp, dp, dp, dp, ctypes.c_int]
             L.or_run.restype = ctypes.c_int
-            L.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, ip, dp, dp,
+            L.or_run.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ip, ip, dp, dp, dp,
                                  ctypes.c_double, dp, ctypes.c_int64, ctypes.c_int64, fp,
                                  ctypes.c_int, ip, lp, lp, dp, ctypes.c_int, ip, dp, ctypes.c_int]
             assert L.or_nfields() == NF and L.or_nparams() == len(PARAMS) and L.or_ngates() == NG
@@ -192,21 +193,34 @@ def gj_csr_sgj(row_ptr, col, w, vd, threads: int = 1) -> np.ndarray:
     return ic
 
 
-def cell_step(S, ic=None, iapp=None, model=None, dt: float = DT_MS, threads: int = 1) -> np.ndarray:
-    """One explicit-Euler cell update of every cell, with the gap current given."""
+def _cell_params(cell_params, n):
+    """Per-cell constants as a contiguous (NCELLPARAMS, n) float64 array, or None."""
+    if cell_params is None:
+        return None
+    cp = np.ascontiguousarray(cell_params, np.float64)
+    assert cp.shape == (NCELLPARAMS, n), cp.shape
+    return cp
+
+
+def cell_step(S, ic=None, iapp=None, model=None, dt: float = DT_MS, threads: int = 1,
+              cell_params=None) -> np.ndarray:
+    """One explicit-Euler cell update of every cell, with the gap current given.
+    cell_params: None or (NCELLPARAMS, n) per-cell constants (table entries 0..19; the
+    g_CaL row is not read, g_CaL being a state field)."""
     S = np.ascontiguousarray(S, np.float64)
     n = S.shape[1]
+    cp = _cell_params(cell_params, n)
     model = model_default() if model is None else np.ascontiguousarray(model, np.float64)
     ic = None if ic is None else np.ascontiguousarray(ic, np.float64)
     iapp = None if iapp is None else np.ascontiguousarray(iapp, np.float64)
     Sn = np.zeros_like(S)
-    lib().or_cell_step(n, _d(model), float(dt), _d(S), _d(ic), _d(iapp), _d(Sn), int(threads))
+    lib().or_cell_step(n, _d(model), _d(cp), float(dt), _d(S), _d(ic), _d(iapp), _d(Sn), int(threads))
     return Sn
 
 
 def run(S0, n_steps: int, kind: int = DENSE, g: float = 0.0, row_ptr=None, col=None, w=None,
         model=None, dt: float = DT_MS, t0: int = 0, iapp_dense=None, pulses=None,
-        trace_cells=None, threads: int = 1):
+        trace_cells=None, threads: int = 1, cell_params=None):
     """Advance S0 (19, n) by n_steps; returns (S_final, trace or None).
 
     pulses: None or a tuple (cell[int32], t_begin[int64], t_end[int64], amp[float64]).
@@ -214,6 +228,7 @@ def run(S0, n_steps: int, kind: int = DENSE, g: float = 0.0, row_ptr=None, col=N
     """
     S = np.array(S0, np.float64, order="C", copy=True)
     n = S.shape[1]
+    cp = _cell_params(cell_params, n)
     model = model_default() if model is None else np.ascontiguousarray(model, np.float64)
     if kind == MATRIX:
         w = np.ascontiguousarray(w, np.float64)
@@ -239,7 +254,7 @@ def run(S0, n_steps: int, kind: int = DENSE, g: float = 0.0, row_ptr=None, col=N
         tr = np.zeros((n_steps, len(tc)), np.float64)
     else:
         tc = tr = None
-    rc = lib().or_run(n, int(kind), float(g), _i(row_ptr), _i(col), _d(w), _d(model), float(dt),
+    rc = lib().or_run(n, int(kind), float(g), _i(row_ptr), _i(col), _d(w), _d(model), _d(cp), float(dt),
                       _d(S), int(t0), int(n_steps), _f(iapp_dense), npul, _i(pc), _l(pb), _l(pe),
                       _d(pa), 0 if tc is None else len(tc), _i(tc), _d(tr), int(threads))
     if rc != 0:

@@ -297,6 +297,21 @@ def test_gap_current_enters_as_outward_dendritic_current(O):
     assert Sf[O.F["V_dend"]].sum() == pytest.approx(-120.0, abs=1e-10)
 
 
+def test_default_state_high_threshold_calcium_current(O):
+    """The default state's I_CaH is the dendritic high-threshold Ca current of the resting
+    state: g_CaH r_inf(-60)^2 (V_0 - V_Ca) = 4.5 r^2 (-60 - 120).  At -60 mV the r gate's
+    alpha = 1.7 / (1 + e^{65/13.9}) = 0.0156873... and its beta (0.02 (V + 8.5) over
+    e^{(V + 8.5)/5} - 1, here -1.03 / (e^{-10.3} - 1)) = 1.0300346..., so r_inf = 0.0150014...
+    and I_CaH = -0.182285 uA/cm^2 (worked out by hand to six figures)."""
+    S = O.default_state(3)
+    r = S[O.F["r"], 0]
+    assert r == pytest.approx(0.0150014, abs=5e-8)
+    assert np.all(S[O.F["I_CaH"]] == pytest.approx(-0.182285, abs=5e-7))
+    P = O.model_default()
+    assert S[O.F["I_CaH"], 0] == pytest.approx(P[O.P["g_CaH"]] * r * r * (P[O.P["V_0"]] - P[O.P["V_Ca"]]), rel=1e-15)
+    assert np.all(S[O.F["I_c"]] == 0.0)
+
+
 # ------------------------------------------------------------------ network invariants
 
 def test_identical_cells_stay_identical(O):
@@ -425,3 +440,61 @@ def test_matrix_two_cells_by_hand_and_symmetric_conservation(O):
     A = rng.uniform(0, 0.05, (80, 80))
     ic = O.gj_matrix(A + A.T, rng.uniform(-70, -40, 80))
     assert abs(ic.sum()) <= 1e-12 * np.abs(ic).sum()
+
+
+# ------------------------------------------------------------------ per-cell constants
+
+def _per_cell_tables(O, n, seed):
+    """n model tables whose per-cell entries (0..19) are the defaults scaled by U(0.7, 1.3)
+    (conductances and area ratios) or shifted by U(-3, 3) mV (reversal potentials)."""
+    rng = np.random.default_rng(seed)
+    base = O.model_default()
+    tabs = np.repeat(base[None, :], n, axis=0)
+    for p in range(O.NCELLPARAMS):
+        if O.PARAMS[p].startswith("V_"):
+            tabs[:, p] += rng.uniform(-3.0, 3.0, n)
+        else:
+            tabs[:, p] *= rng.uniform(0.7, 1.3, n)
+    return tabs
+
+
+def test_per_cell_constants_equal_to_the_table_change_nothing(O):
+    n = 40
+    cfg = inputs.config("c1")
+    S = O.default_state(n)
+    S[O.F["V_dend"]] += inputs.vdend_jitter(n, 4)
+    cp = np.repeat(O.model_default()[:O.NCELLPARAMS, None], n, axis=1)
+    a, _ = O.run(S, 200, kind=O.DENSE, g=0.01, pulses=inputs.pulses(np.arange(8), 2.0, 6.0, 6.0))
+    b, _ = O.run(S, 200, kind=O.DENSE, g=0.01, pulses=inputs.pulses(np.arange(8), 2.0, 6.0, 6.0), cell_params=cp)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_per_cell_constants_equal_one_table_per_cell(O):
+    """Uncoupled cells with per-cell constants evolve exactly as each cell run alone with a
+    model table holding its constants (brute force over the cells; catches a transposed or
+    shifted per-cell layout)."""
+    n = 9
+    tabs = _per_cell_tables(O, n, 11)
+    S = O.default_state(n)
+    S[O.F["V_dend"]] += inputs.vdend_jitter(n, 5)
+    S[O.F["g_CaL"]] = np.linspace(0.5, 1.1, n)
+    pul = inputs.pulses(np.arange(n), 1.0, 4.0, 6.0)
+    cp = tabs[:, :O.NCELLPARAMS].T.copy()
+    cp[O.P["g_CaL"]] = 1e9            # never read: g_CaL comes from the state
+    got, _ = O.run(S, 300, kind=O.NOGJ, pulses=pul, cell_params=cp)
+    for i in range(n):
+        ref, _ = O.run(S[:, i:i + 1], 300, kind=O.NOGJ, model=tabs[i],
+                       pulses=inputs.pulses(np.array([0]), 1.0, 4.0, 6.0))
+        np.testing.assert_array_equal(got[:, i], ref[:, 0])
+
+
+def test_per_cell_leak_conductance_hand_step(O):
+    """A leak-only cell whose own g_ld is doubled: one step moves V_dend twice as far
+    towards V_L as in a cell with the table's g_ld (by hand: 0.05 * 0.016 * 70 = 0.056 mV)."""
+    P = _model_only(O, keep=("g_ld",))
+    S = _state(O, 2, V_dend=-60.0, V_soma=-60.0, V_axon=-60.0, g_CaL=0.0)
+    cp = np.repeat(P[:O.NCELLPARAMS, None], 2, axis=1)
+    cp[O.P["g_ld"], 1] *= 2.0
+    Sn = O.cell_step(S, model=P, cell_params=cp)
+    assert Sn[O.F["V_dend"], 0] == pytest.approx(-59.944, abs=1e-13)
+    assert Sn[O.F["V_dend"], 1] == pytest.approx(-59.888, abs=1e-13)
