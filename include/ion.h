@@ -43,6 +43,7 @@ extern "C" {
 #define ION_NFIELDS 19 /* Table "reqs": 19 state words per cell */
 #define ION_NPARAMS 25 /* model constants, order of enum ion_param */
 #define ION_NGATES 12  /* gating variables with a rate function */
+#define ION_NCELLPARAMS 20 /* per-cell model constants: entries 0..19 of enum ion_param */
 
 typedef enum {
     ION_OK = 0,
@@ -68,7 +69,10 @@ enum ion_field {
     ION_FIELD_ALL = -1                           /* all 19 fields, SoA order    */
 };
 
-/* Model constants (the "20 conductances" of Table "reqs" are entries 0..19). */
+/* Model constants.  Entries 0..19 are the per-cell constants a neuron may own (see
+ * ion_params.cell_params): 13 conductances (g_int and the 12 channel conductances), the two
+ * area ratios p1, p2 and five reversal potentials.  Table "reqs" counts 20 conductances per
+ * neuron; the three-compartment model used here has 13. */
 enum ion_param {
     ION_P_GINT = 0, ION_P_P1, ION_P_P2,
     ION_P_GCAH, ION_P_GKCA, ION_P_GH, ION_P_GLD,
@@ -152,6 +156,22 @@ typedef struct {
     int64_t debug_delay_ns;     /* test hook, 0 in production: with ION_FLAG_PERSISTENT one CTA
                                    sleeps this long before its first grid barrier (a short
                                    barrier_timeout_ns then yields ION_ERR_TIMEOUT)          */
+    const float *cell_params;   /* per-cell model constants (Table "reqs": every neuron has its
+                                   own conductances), or NULL for the model table's values in
+                                   every cell.  Host FP32 array of ION_NCELLPARAMS x n_cells,
+                                   structure of arrays: entry p of cell i at p * n_cells + i,
+                                   p in enum ion_param order (g_int, p1, p2, the 12 channel
+                                   conductances, V_Na, V_K, V_Ca, V_h, V_L).  Copied at
+                                   creation; checked finite, 0 < p1, p2 < 1.  Entry ION_P_GCAL
+                                   is not read: g_CaL is per cell already (state field
+                                   ION_G_CAL).  Dense uniform, CSR and NO_GJ networks only; with
+                                   gap junctions the currents and the cell update then run as
+                                   two launches per step (as ION_FLAG_SPLIT).  Not with
+                                   PERSISTENT, SURROGATE, SGJ, a dense matrix or batches
+                                   (ION_ERR_UNSUPPORTED)                                   */
+    uint32_t debug_barrier_base;/* test hook, 0 in production: the value the grid-barrier
+                                   arrival counter of a persistent launch starts from, so that
+                                   a test can make it wrap past 2^32 within a few steps     */
 } ion_params;
 
 /* Evoked input (Sec. 2.2: one evoked-input word per cell per step).
@@ -327,7 +347,10 @@ void ion_destroy(ion_sim *sim);
 
 /* Ic[i] = g_c * sum_j (0.8 e^{-(V_i-V_j)^2/100} + 0.2)(V_i - V_j) for a dense uniform
  * network (Algorithm 1 with C = 100 %).  vdend, ic: device arrays of n floats.
- * kahan != 0 compensates the j sums. */
+ * kahan != 0 compensates the j sums.  The launch stages V_dend into shared memory with
+ * bulk copies whose completion it waits for with a bound (about 0.5 s); should a copy not
+ * land in time, the rows of the affected thread blocks receive NaN instead of a current
+ * (this entry point has no status word to report it otherwise). */
 ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, float *ic, int32_t kahan,
                         void *cuda_stream);
 
@@ -344,7 +367,10 @@ ion_status ion_gj_dense(const float *vdend, int32_t n, float g_c, float *ic, int
  * 65536; a larger n returns ION_ERR_INVALID_ARG without touching the device.
  * Arguments, layout and result are those of ion_gj_dense.
  * The first call on each device looks up the array's device address with that device
- * current: make that first call before starting any stream capture.
+ * current: make that first call before starting any stream capture.  The address is kept
+ * with the identity of the device's context; after a device reset (which gives the device
+ * a new context and reloads the library's device code) the next call looks it up again,
+ * so that call too belongs outside a capture.
  * Every call on a device shares the one array and leaves its contents behind; each call
  * rewrites the whole range it reads, so nothing needs clearing between calls.  Calls
  * whose work can overlap on the GPU (other streams, other host threads) race on the

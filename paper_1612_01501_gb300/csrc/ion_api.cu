@@ -92,6 +92,30 @@ ModelF ion_model_to_f32(const ion_model &m, double dt) {
     return P;
 }
 
+// Per-cell constants (host, ION_NCELLPARAMS x n in ion_param order) to the kernels' per-cell
+// rows (ModelF members 0..19, FP32, derived coupling conductances computed in double).
+// The g_CaL row is not read.  Rejects non-finite values and area ratios outside (0, 1).
+ion_status ion_cell_params_to_f32(const float *cp, int32_t n, const ion_model &m, double dt, std::vector<float> &out) {
+    out.assign((size_t)NCELLP * n, 0.0f);
+    for (int32_t i = 0; i < n; ++i) {
+        ion_model q = m;
+        for (int p = 0; p < ION_NCELLPARAMS; ++p) {
+            if (p == ION_P_GCAL) continue;
+            const float v = cp[(size_t)p * n + i];
+            if (!std::isfinite(v))
+                return ion_fail(nullptr, ION_ERR_INVALID_ARG, "per-cell constant %d of cell %d not finite", p, i);
+            q.v[p] = v;
+        }
+        if (!(q.v[ION_P_P1] > 0 && q.v[ION_P_P1] < 1 && q.v[ION_P_P2] > 0 && q.v[ION_P_P2] < 1))
+            return ion_fail(nullptr, ION_ERR_INVALID_ARG, "per-cell area ratios of cell %d outside (0, 1)", i);
+        const ModelF P = ion_model_to_f32(q, dt);
+        const float row[NCELLP] = {P.g_ds, P.g_sd, P.g_sa, P.g_as, P.gCaH, P.gKCa, P.gh, P.gld, P.gNas, P.gKdrs,
+                                   P.gKs, P.gls, P.gNaa, P.gKa, P.gla, P.VNa, P.VK, P.VCa, P.Vh, P.VL};
+        for (int k = 0; k < NCELLP; ++k) out[(size_t)k * n + i] = row[k];
+    }
+    return ION_OK;
+}
+
 static bool model_valid(const ion_model &m) {
     for (double x : m.v)
         if (!std::isfinite(x)) return false;
@@ -360,6 +384,8 @@ void ion_sim_free_device(ion_sim *s) {
     cudaFree(s->d_iapp);
     cudaFree(s->d_trace);
     cudaFree(s->d_ic);
+    cudaFree(s->d_cellp);
+    s->d_cellp = nullptr;
     cudaFree(s->d_mid);
     cudaFree(s->d_mlp);
     s->extra_free(s);
@@ -405,6 +431,15 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
     if (!model_valid(m)) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: invalid model table");
     if (params->flags & ION_FLAG_SURROGATE) {
         if (!params->surrogate) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create: SURROGATE flag without weights");
+    }
+    std::vector<float> cellp;   // per-cell constants in the kernels' order (ModelF members 0..19)
+    if (params->cell_params) {
+        if (net->kind == ION_DENSE_MATRIX ||
+            (params->flags & (ION_FLAG_PERSISTENT | ION_FLAG_SURROGATE | ION_FLAG_SGJ)))
+            return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create: per-cell constants need a dense uniform, CSR "
+                            "or NO_GJ network without PERSISTENT, SURROGATE or SGJ");
+        const ion_status cst = ion_cell_params_to_f32(params->cell_params, net->n_cells, m, dt, cellp);
+        if (cst != ION_OK) return cst;
     }
 
     ion_sim *s = new (std::nothrow) ion_sim();
@@ -561,6 +596,16 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
         s->lps = s->n <= SGJ_ONE_LAUNCH ? 1 : 2;   // (partial sums +) update
         e = ion_alloc(&s->d_sgj, (size_t)sgj_partials(s->n) * sizeof(float));
         if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_OOM, "ion_create: %s", cudaGetErrorString(e)));
+    }
+    if (!cellp.empty()) {   // per-cell constants: read by the stand-alone cell update
+        if (s->kind != ION_NO_GJ) s->flags |= ION_FLAG_SPLIT;
+        e = ion_alloc(&s->d_cellp, (size_t)NCELLP * s->stride * sizeof(float));
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(s->d_cellp, s->stride * sizeof(float), cellp.data(), s->n * sizeof(float),
+                                  s->n * sizeof(float), NCELLP, cudaMemcpyHostToDevice, s->st);
+        if (e != cudaSuccess)
+            return fail(ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA,
+                                 "ion_create: per-cell constants: %s", cudaGetErrorString(e)));
     }
     if ((s->flags & ION_FLAG_SPLIT) && s->kind != ION_NO_GJ) {
         s->lps = 2;
@@ -737,7 +782,7 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
         e = launch_dense_step(a, s->dense_R, s->dense_W, s->dense_GJ, s->st);
         s->launches++;
         if (e == cudaSuccess && split) {
-            CellArgs ca{c, s->d_ic};
+            CellArgs ca{c, s->d_ic, s->d_cellp};
             e = launch_cell_step(ca, s->st);
             s->launches++;
         }
@@ -754,12 +799,12 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
             e = launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);
         s->launches++;
         if (e == cudaSuccess && split) {
-            CellArgs ca{c, s->d_ic};
+            CellArgs ca{c, s->d_ic, s->d_cellp};
             e = launch_cell_step(ca, s->st);
             s->launches++;
         }
     } else {
-        CellArgs ca{c, nullptr};
+        CellArgs ca{c, nullptr, s->d_cellp};
         e = launch_cell_step(ca, s->st);
         s->launches++;
     }

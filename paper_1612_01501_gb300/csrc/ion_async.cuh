@@ -84,11 +84,19 @@ __device__ __forceinline__ void red_release_gpu_add(uint32_t *p, uint32_t v) {
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// true once the 32-bit arrival counter has reached `target`, comparing modulo 2^32: a long
+// persistent launch arrives more than 2^32 times in total, so both the counter and the
+// targets wrap; the two never drift apart by 2^31 (the counter exceeds the current target
+// by at most the grid size), so the sign of their difference decides
+__device__ __forceinline__ bool arrivals_reached(uint32_t count, uint32_t target) {
+    return (int32_t)(count - target) >= 0;
+}
+
 // Every CTA arrives once per barrier on a monotonically increasing counter (zeroed before
-// the launch); barrier k completes when the counter reaches k * gridDim.x.  A wait that
-// exceeds timeout_ns (or 2^30 polls) sets `status` bit 2 (timeout) and the shared abort
-// word, so every other CTA leaves its own wait too; the function then returns false in
-// every thread of the CTA.
+// the launch); barrier k completes when the counter reaches k * gridDim.x (mod 2^32).  A
+// wait that exceeds timeout_ns (or 2^30 polls) sets `status` bit 2 (timeout) and the shared
+// abort word, so every other CTA leaves its own wait too; the function then returns false
+// in every thread of the CTA.
 __device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *abort_flag, uint32_t target,
                                              uint64_t timeout_ns, uint32_t *status, int *ok_sh) {
     __syncthreads();
@@ -97,10 +105,10 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *abort_fl
         // release at GPU scope: the CTA's writes, ordered before this by the bar.sync above,
         // become visible before the arrival does
         red_release_gpu_add(count, 1u);
-        if (ld_acquire_gpu(count) < target) {
+        if (!arrivals_reached(ld_acquire_gpu(count), target)) {
             const uint64_t t0 = globaltimer_ns();
             for (uint32_t it = 1;; ++it) {
-                if (ld_acquire_gpu(count) >= target) break;
+                if (arrivals_reached(ld_acquire_gpu(count), target)) break;
                 if ((it & 63u) == 0u) {          // the abort word and the clock every 64 polls
                     if (ld_acquire_gpu(abort_flag) != 0u) {
                         ok = 0;

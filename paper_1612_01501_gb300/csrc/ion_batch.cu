@@ -441,6 +441,8 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
         return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad arguments");
     if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_PERSISTENT | ION_FLAG_SPLIT | ION_FLAG_SGJ))
         return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: flags not supported for batches");
+    if (params->cell_params)
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: per-cell constants not supported for batches");
     // validate and lay out
     std::vector<BatchNet> bn((size_t)n_nets);
     int64_t seg = 0, n_user = 0, nnz_total = 0;

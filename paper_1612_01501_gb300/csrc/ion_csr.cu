@@ -466,7 +466,8 @@ __global__ void __launch_bounds__(256) cell_step_kernel(const CellArgs a) {
     const float ic = a.ic != nullptr ? a.ic[i] : 0.0f;
     float iapp = pulse_current(c.pulses, i, t);
     if (c.iapp != nullptr) iapp += c.iapp[i];
-    const CellNext o = cell_step(c.P, cell, ic, iapp);
+    const CellNext o = a.cellp != nullptr ? cell_step(cell_model(c.P, a.cellp, c.S.stride, i), cell, ic, iapp)
+                                          : cell_step(c.P, cell, ic, iapp);
     finish_cell(c, t, vnext, i, o);
 }
 

@@ -86,6 +86,10 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
             // let any copy still in flight land before the CTA's shared memory is released
             for (int k = 0; k < 2 && k < sm.n_tiles; ++k) (void)mbar_wait_bounded(&bar[k], uses[k] & 1u);
         }
+        // the stand-alone primitive has no status word: its caller sees NaN in these rows
+        if (!a.fuse)
+            for (int rr = threadIdx.x; rr < rows_cta && row_base + rr < n; rr += blockDim.x)
+                a.ic_out[row_base + rr] = __int_as_float(0x7fc00000);
         return;
     }
     const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, cs, lane, red_s, red_c, &U_sh);
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kerne
             __syncthreads();
         } else {
             if (row_thread) vd_slot(c.S, t + 1)[my_row] = cell.vd;
-            ok = grid_barrier(a.bar_count, a.abort_flag, (uint32_t)(k + 1) * gridDim.x, a.timeout_ns, c.status,
+            ok = grid_barrier(a.bar_count, a.abort_flag, a.bar_base + (uint32_t)(k + 1) * gridDim.x, a.timeout_ns, c.status,
                               &ok_sh);
         }
     }

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(896) dense_half_kernel(const HalfArgs a) {
     }
 
     bool ok = true;
-    uint32_t bar_target = 0;
+    uint32_t bar_target = a.bar_base;
     for (int k = 0; k < a.n_steps && ok; ++k) {
         const int64_t t = t0 + k;
         const float *vcur = vd_slot(c.S, t);

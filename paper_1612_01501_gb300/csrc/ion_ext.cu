@@ -10,13 +10,22 @@
 using namespace ion;
 
 // ---- persistent dense launches ----------------------------------------------------------
+// Arrival counter := barrier_base (0 unless a test moved it near 2^32), abort word := 0.
+// The barriers compare the counter with their targets modulo 2^32, so a launch may run
+// any number of steps whatever the base.
+static cudaError_t reset_barrier(ion_sim *s) {
+    s->bar_init[0] = s->barrier_base;
+    s->bar_init[1] = 0u;
+    return cudaMemcpyAsync(s->d_bar, s->bar_init, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, s->st);
+}
+
 // Multi-CTA networks use the half-work kernel (each unordered pair once, two barriers per
 // step); one-CTA networks the full-work kernel with V_dend kept in shared memory.
 static ion_status half_run(ion_sim *s, int64_t n_steps, const float *iapp) {
     (void)iapp;
     int64_t done = 0;
     while (done < n_steps) {
-        const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 22);   // 2 * chunk * grid < 2^32
+        const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 22);
         HalfArgs a{};
         a.c = ion_step_common(s, 0, nullptr);
         a.c.par = -1;   // many steps per launch: the slots follow the device counter
@@ -27,10 +36,11 @@ static ion_status half_run(ion_sim *s, int64_t n_steps, const float *iapp) {
         a.abort_flag = s->d_bar + 1;
         a.timeout_ns = s->barrier_timeout_ns;
         a.debug_delay_ns = s->debug_delay_ns;
+        a.bar_base = s->barrier_base;
         a.colsum = s->d_half;
         a.colsum_stride = s->half_stride;
         a.usum = s->d_half + (int64_t)s->half_grid * s->half_stride;
-        cudaError_t e = cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(uint32_t), s->st);
+        cudaError_t e = reset_barrier(s);
         if (e == cudaSuccess)
             e = launch_dense_half(a, s->persist_R, s->persist_W, s->persist_GJ, s->half_grid, true, nullptr, s->st);
         s->launches++;
@@ -57,7 +67,8 @@ static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
         a.abort_flag = s->d_bar + 1;
         a.timeout_ns = s->barrier_timeout_ns;
         a.debug_delay_ns = s->debug_delay_ns;
-        cudaError_t e = cudaMemsetAsync(s->d_bar, 0, 2 * sizeof(uint32_t), s->st);
+        a.bar_base = s->barrier_base;
+        cudaError_t e = reset_barrier(s);
         if (e == cudaSuccess) e = persist_dense(a, s->persist_R, s->persist_W, s->persist_GJ, nullptr, true, s->st);
         s->launches++;
         if (e == cudaSuccess) e = launch_advance(s->d_t, chunk, s->st);
@@ -97,6 +108,7 @@ static bool choose_persist_shape(ion_sim *s) {
 
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
     s->debug_delay_ns = p->debug_delay_ns;
+    s->barrier_base = p->debug_barrier_base;
     if (s->flags & ION_FLAG_SURROGATE) return ion_setup_surrogate(s, p);
     if ((s->flags & ION_FLAG_PERSISTENT) && s->kind == ION_DENSE_UNIFORM && !(s->flags & ION_FLAG_SPLIT)) {
         int coop = 0;

@@ -109,20 +109,22 @@ struct PersistArgs {
     float g;
     int32_t n_steps;
     int32_t kahan;
-    uint32_t *bar_count;  // grid-barrier arrivals (zeroed before the launch)
+    uint32_t *bar_count;  // grid-barrier arrivals (set to bar_base before the launch)
     uint32_t *abort_flag; // set by a CTA whose wait timed out (zeroed before the launch)
     uint64_t timeout_ns;  // bound on one grid-barrier wait
     int64_t debug_delay_ns;  // test hook: the last CTA sleeps this long before its first step
+    uint32_t bar_base;    // the arrival counter's value at launch (0; a test hook sets others)
 };
 struct HalfArgs {
     StepCommon c;          // k_off unused: the launch runs steps *t_dev .. *t_dev + n_steps - 1
     float g;
     int32_t n_steps;
     int32_t rows;          // rows per CTA (the block size b)
-    uint32_t *bar_count;   // grid-barrier arrivals (zeroed before the launch)
+    uint32_t *bar_count;   // grid-barrier arrivals (set to bar_base before the launch)
     uint32_t *abort_flag;
     uint64_t timeout_ns;
     int64_t debug_delay_ns;
+    uint32_t bar_base;     // the arrival counter's value at launch
     float *colsum;         // [grid][colsum_stride] column sums of each CTA's tile (L2-resident)
     int32_t colsum_stride;
     float *usum;           // [grid] sum of u over each CTA's own rows
@@ -135,6 +137,8 @@ struct MatrixArgs {
 struct CellArgs {
     StepCommon c;
     const float *ic;      // NULL: no gap current
+    const float *cellp;   // NULL, or per-cell constants: NCELLP x c.S.stride floats, row k
+                          // holding member k of ModelF (g_ds ... VL) for every cell
 };
 
 // launchers (return the CUDA launch status)

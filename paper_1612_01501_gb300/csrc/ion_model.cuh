@@ -45,6 +45,38 @@ struct ModelF {
     float dt;      // dt (gates and [Ca])
     float ca_in, ca_out;
 };
+// A cell may own the first NCELLP members of ModelF (g_ds ... VL): Table "reqs" gives
+// every neuron its own conductances.
+constexpr int NCELLP = 20;
+
+// The model constants of cell i: the shared ones with the cell's own first NCELLP members
+// (row k of cp, stride floats per row).
+__device__ __forceinline__ ModelF cell_model(const ModelF &P, const float *__restrict__ cp, int64_t stride,
+                                             int64_t i) {
+    ModelF q = P;
+    const float *c = cp + i;
+    q.g_ds = c[0 * stride];
+    q.g_sd = c[1 * stride];
+    q.g_sa = c[2 * stride];
+    q.g_as = c[3 * stride];
+    q.gCaH = c[4 * stride];
+    q.gKCa = c[5 * stride];
+    q.gh = c[6 * stride];
+    q.gld = c[7 * stride];
+    q.gNas = c[8 * stride];
+    q.gKdrs = c[9 * stride];
+    q.gKs = c[10 * stride];
+    q.gls = c[11 * stride];
+    q.gNaa = c[12 * stride];
+    q.gKa = c[13 * stride];
+    q.gla = c[14 * stride];
+    q.VNa = c[15 * stride];
+    q.VK = c[16 * stride];
+    q.VCa = c[17 * stride];
+    q.Vh = c[18 * stride];
+    q.VL = c[19 * stride];
+    return q;
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

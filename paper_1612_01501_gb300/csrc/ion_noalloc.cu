@@ -12,7 +12,10 @@
 // (NOALLOC_MAX_CELLS floats = 256 KiB per device).  Host code cannot pass the array's
 // name to a kernel (on the host that name is only a stand-in, not a device address), so
 // the first call on each device looks up its device address with cudaGetSymbolAddress,
-// with that device current, and caches it.
+// with that device current, and caches it together with the identity of the device's
+// context.  A device reset destroys the context and the module with it; the next call
+// sees a different context and looks the address up again (that call, like the first,
+// should come before any stream capture).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -28,19 +31,59 @@ constexpr int MAX_DEVICES = 64;
 
 static __device__ __align__(256) float g_noalloc_vdend[NOALLOC_MAX_CELLS];
 
-std::mutex g_noalloc_mu;
-float *g_noalloc_ptr[MAX_DEVICES] = {};
+// Driver entry points that identify the current context (resolved through the runtime,
+// so the library needs no link-time dependence on the driver library).  Both return a
+// CUresult (0 = success); a context is an opaque pointer.
+using CtxGetCurrentFn = int (*)(void **);
+using CtxGetIdFn = int (*)(void *, unsigned long long *);
 
-// Device address of this device's copy of the array (looked up once per device).
+struct Slot {
+    float *ptr = nullptr;            // device address of this device's array
+    unsigned long long ctx_id = 0;   // the context it belongs to (0: unknown)
+};
+
+std::mutex g_noalloc_mu;
+Slot g_slot[MAX_DEVICES];
+bool g_resolved = false;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// Unique id of the calling thread's current context, or 0 where the driver cannot tell.
+unsigned long long current_ctx_id() {
+    if (!g_resolved) {
+        g_resolved = true;
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_ctx_id = reinterpret_cast<CtxGetIdFn>(f);
+    }
+    void *ctx = nullptr;
+    unsigned long long id = 0;
+    if (g_ctx_current == nullptr || g_ctx_id == nullptr || g_ctx_current(&ctx) != 0 || ctx == nullptr ||
+        g_ctx_id(ctx, &id) != 0)
+        return 0;
+    return id;
+}
+
+// Device address of this device's copy of the array: looked up once per device and
+// context (again after a reset gave the device a new context).
 cudaError_t noalloc_scratch(int dev, float **out) {
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (g_noalloc_ptr[dev] == nullptr) {
+    Slot &sl = g_slot[dev];
+    const unsigned long long id = current_ctx_id();
+    if (sl.ptr == nullptr || (id != 0 && id != sl.ctx_id)) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_vdend);
         if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = static_cast<float *>(p);
+        sl.ptr = static_cast<float *>(p);
+        sl.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = sl.ptr;
     return cudaSuccess;
 }
 

@@ -27,6 +27,7 @@ struct ion_sim {
     // state and bookkeeping
     float *d_state = nullptr;       // 20 * stride floats
     float *d_ic = nullptr;          // gap currents (split mode)
+    float *d_cellp = nullptr;       // per-cell constants, NCELLP rows of stride floats (or NULL)
     int64_t *d_t = nullptr;         // device step counter
     uint32_t *d_status = nullptr;   // sticky status bits
     uint32_t sticky = 0;            // status bits seen by the host
@@ -60,6 +61,8 @@ struct ion_sim {
     uint64_t barrier_timeout_ns = 0;
     int64_t debug_delay_ns = 0;
     uint32_t *d_bar = nullptr;      // grid barrier counter + abort word (persistent launches)
+    uint32_t barrier_base = 0;      // the counter's value at each persistent launch (test hook)
+    uint32_t bar_init[2] = {0u, 0u};   // host source of the counter reset (lives with the handle)
     int persist_R = 0, persist_W = 0, persist_GJ = 1;
     float *d_half = nullptr;        // half-work persistent kernel: column sums + per-CTA sums of u
     int half_grid = 0, half_stride = 0;
@@ -102,6 +105,7 @@ void ion_csr_fill(const ion_sim *s, ion::CsrArgs &a, bool staged);
 ion_status ion_prepare_csr_chunk(ion_sim *s);
 ion_status ion_fail(ion_sim *s, ion_status code, const char *fmt, ...);
 ion::ModelF ion_model_to_f32(const ion_model &m, double dt);
+ion_status ion_cell_params_to_f32(const float *cp, int32_t n, const ion_model &m, double dt, std::vector<float> &out);
 ion::StepCommon ion_step_common(ion_sim *s, int k_off, const float *iapp);
 float *ion_field_ptr(ion_sim *s, int32_t field);
 ion_status ion_validate_csr(int32_t n, const ion_conn *c);

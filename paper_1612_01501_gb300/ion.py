@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libion.so")
 
-NFIELDS, NPARAMS, NGATES = 19, 25, 12
+NFIELDS, NPARAMS, NGATES, NCELLPARAMS = 19, 25, 12, 20
 FIELDS = ("V_dend", "V_soma", "V_axon", "Ca", "r", "s", "q", "k", "l", "m_s", "h_s", "n_s", "x_s",
           "m_a", "h_a", "x_a", "g_CaL", "I_CaH", "I_c")
 FIELD = {f: i for i, f in enumerate(FIELDS)}
@@ -62,7 +62,8 @@ class ion_params(ctypes.Structure):
     _fields_ = [("dt_ms", ctypes.c_double), ("model", ctypes.POINTER(ion_model)), ("flags", ctypes.c_uint32),
                 ("surrogate", ctypes.c_void_p), ("check_every", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
                 ("barrier_timeout_ns", ctypes.c_uint64), ("cuda_stream", ctypes.c_void_p),
-                ("tune", ctypes.c_void_p), ("debug_delay_ns", ctypes.c_int64)]
+                ("tune", ctypes.c_void_p), ("debug_delay_ns", ctypes.c_int64), ("cell_params", c_f32p),
+                ("debug_barrier_base", ctypes.c_uint32)]
 
 
 class ion_input(ctypes.Structure):
@@ -235,7 +236,8 @@ def _conn_struct(kind, g=0.0, row_ptr=None, col=None, w=None):
 
 
 def _params_struct(dt_ms=0.05, model=None, flags=FLAG_KAHAN, stream=None, graph_steps=0, tune=None,
-                   surrogate=None, check_every=0, barrier_timeout_ns=0, debug_delay_ns=0):
+                   surrogate=None, check_every=0, barrier_timeout_ns=0, debug_delay_ns=0, cell_params=None,
+                   debug_barrier_base=0):
     p = ion_params()
     p.dt_ms = float(dt_ms)
     m = _model_struct(model)
@@ -245,8 +247,14 @@ def _params_struct(dt_ms=0.05, model=None, flags=FLAG_KAHAN, stream=None, graph_
     p.check_every = int(check_every)
     p.barrier_timeout_ns = int(barrier_timeout_ns)
     p.debug_delay_ns = int(debug_delay_ns)
+    p.debug_barrier_base = int(debug_barrier_base) & 0xFFFFFFFF
     p.cuda_stream = ctypes.c_void_p(stream) if stream else None
     keep = [m]
+    if cell_params is not None:   # (NCELLPARAMS, n) host array, ion_param row order
+        cp = np.ascontiguousarray(cell_params, np.float32)
+        assert cp.ndim == 2 and cp.shape[0] == NCELLPARAMS
+        p.cell_params = _ptr(cp, ctypes.c_float)
+        keep.append(cp)
     if tune is not None:
         t = ion_tune(*[int(tune.get(k, 0)) for k, _ in ion_tune._fields_])
         p.tune = ctypes.cast(ctypes.pointer(t), ctypes.c_void_p)

@@ -122,27 +122,75 @@ def test_batch_one_step_error(cuda, O, layout):
         off += n
 
 
-def test_c4_batch_of_256_sampled_against_oracle(cuda, O):
-    specs = inputs.batch_specs()
-    nets = _nets(specs)
+def _c4_spread(nets, per_kind=16):
+    """Indices of `per_kind` dense and `per_kind` CSR networks of the 256-network batch at
+    evenly spaced size ranks (smallest and largest of each kind included)."""
+    pick = []
+    for kind in ("dense", "csr"):
+        idx = sorted((i for i, b in enumerate(nets) if b["kind"] == kind), key=lambda i: nets[i]["n"])
+        ranks = np.unique(np.round(np.linspace(0, len(idx) - 1, per_kind)).astype(int))
+        pick += [idx[r] for r in ranks]
+    return pick
+
+
+def test_c4_all_256_networks_one_step(cuda, O):
+    """One step of every network of the 256-network batch from an identical FP32 state,
+    each against the oracle run of that network alone (per-step relative error bar)."""
+    nets = _nets(inputs.batch_specs())
     S0, pul = _batch_inputs(O, nets)
     h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, graph_steps=50)
     try:
-        ion.ion_set_input(h, pul)
-        ion.ion_step(h, 200)
+        ion.ion_step(h, 1)
         got = ion.ion_read_state(h, S0.shape[1])
     finally:
         ion.ion_destroy(h)
     offs = np.concatenate([[0], np.cumsum([b["n"] for b in nets])])
-    dense = [i for i, b in enumerate(nets) if b["kind"] == "dense"]
-    csr = [i for i, b in enumerate(nets) if b["kind"] == "csr"]
-    pick = [min(dense, key=lambda i: nets[i]["n"]), min(csr, key=lambda i: nets[i]["n"]),
-            max(csr, key=lambda i: nets[i]["n"]), sorted(dense, key=lambda i: nets[i]["n"])[len(dense) // 2]]
-    for i in pick:
-        b = nets[i]
-        ref = _oracle_net(O, b, S0[:, offs[i]:offs[i + 1]], 200, b["pulses"])
-        assert np.abs(got[:3, offs[i]:offs[i + 1]] - ref[:3]).max() <= TRAJ_MV, b["spec"]
-    assert np.all(np.isfinite(got))
+    worst = 0.0
+    for i, b in enumerate(nets):
+        sl = slice(offs[i], offs[i + 1])
+        ref = _oracle_net(O, b, S0[:, sl], 1, None)
+        if b["kind"] == "dense":
+            scale = b["g"] * sum_abs_dv(S0[0, sl])
+        else:
+            scale = csr_abs_scale(b["row_ptr"], b["col"], b["w"], S0[0, sl])
+        err = step_rel_err(got[:, sl], ref, scale)
+        assert err.max() <= STEP_RTOL, (i, b["spec"], err.max(axis=1))
+        worst = max(worst, float(err.max()))
+    print(f"256 networks, one step: worst relative error {worst:.2e}")
+
+
+def test_c4_trajectories_100ms_on_32_networks(cuda, O):
+    """The whole batch for 100 ms (2000 steps, pulses at 20-30 ms) in graph replays;
+    16 dense and 16 CSR networks spanning the size range stay within 0.1 mV of their
+    oracle runs at every 25 ms checkpoint."""
+    nets = _nets(inputs.batch_specs())
+    S0, pul = _batch_inputs(O, nets)
+    offs = np.concatenate([[0], np.cumsum([b["n"] for b in nets])])
+    pick = _c4_spread(nets)
+    assert len(pick) == 32
+    refs = {i: S0[:, offs[i]:offs[i + 1]].astype(np.float64) for i in pick}
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, graph_steps=50)
+    worst = 0.0
+    try:
+        ion.ion_set_input(h, pul)
+        t = 0
+        for _ in range(4):
+            ion.ion_step(h, 500)
+            got = ion.ion_read_state(h, S0.shape[1])
+            assert np.all(np.isfinite(got))
+            for i in pick:
+                b = nets[i]
+                kind = {"dense": O.DENSE, "csr": O.CSR}[b["kind"]]
+                refs[i], _ = O.run(refs[i], 500, kind=kind, g=b.get("g", 0.0), row_ptr=b.get("row_ptr"),
+                                   col=b.get("col"), w=None if b.get("w") is None else b["w"].astype(np.float64),
+                                   t0=t, pulses=b["pulses"], threads=max(1, O.max_threads()))
+                d = np.abs(got[:3, offs[i]:offs[i + 1]] - refs[i][:3]).max()
+                assert d <= TRAJ_MV, (t + 500, i, b["spec"], d)
+                worst = max(worst, float(d))
+            t += 500
+    finally:
+        ion.ion_destroy(h)
+    print(f"32 networks over 100 ms: worst |dV| {worst:.2e} mV")
 
 
 def test_autotune_leaves_state_untouched_and_results_agree(cuda, O):

@@ -126,3 +126,17 @@ def test_half_work_barrier_timeout_is_reported(cuda, O):
         with pytest.raises(ion.IonError) as ei:
             sim.sync()
         assert ei.value.status == ion.ERR_TIMEOUT
+
+
+@pytest.mark.parametrize("half", [False, True])
+def test_grid_barrier_counter_wraps_past_2_to_32(cuda, O, half):
+    """The barrier's 32-bit arrival counter starts 300 arrivals below 2^32 (test hook), so it
+    and the barrier targets wrap within the first steps, as they do after ~2^32 arrivals of
+    a long launch.  The comparison is modulo 2^32: the states equal those of a launch whose
+    counter starts at 0, bit for bit."""
+    cfg = inputs.config("c2")
+    S0 = initial_state(O, cfg)
+    flags = ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | (ion.FLAG_HALF_WORK if half else 0)
+    a, _ = _run(cfg["n"], cfg["g"], S0, 200, flags, chunks=2)
+    b, _ = _run(cfg["n"], cfg["g"], S0, 200, flags, chunks=2, debug_barrier_base=(1 << 32) - 300)
+    np.testing.assert_array_equal(a, b)

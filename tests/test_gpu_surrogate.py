@@ -44,9 +44,14 @@ def test_training_gradients_match_fp64_oracle(cuda, B):
     p32 = {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
     Lr, gr = mlp.loss_and_grads(p32, x.astype(np.float64), t.astype(np.float64), mask.astype(np.float64))
     assert L == pytest.approx(Lr, rel=1e-5)
+    # every entry: |g - g_ref| <= 1e-4 |g_ref| + 1e-6 max|g_ref of its block|.  The floor is
+    # the FP32 rounding of a sum of B sample terms (about B * 2^-24 of the largest term, so
+    # 2e-5 at B = 300); a wrong entry, even a single bias, exceeds it
     for k in ("w1", "b1", "w2", "b2", "w3", "b3"):
-        rel = np.linalg.norm(g[k] - gr[k]) / np.linalg.norm(gr[k])
-        assert rel <= 1e-4, (k, rel)
+        scale = np.abs(gr[k]).max()
+        err = np.abs(g[k] - gr[k]) - (1e-4 * np.abs(gr[k]) + 1e-6 * scale)
+        worst = np.unravel_index(np.argmax(err), err.shape)
+        assert err.max() <= 0.0, (k, worst, float(g[k][worst]), float(gr[k][worst]), scale)
 
 
 def test_tensor_core_inference_matches_fp64_forward(cuda):

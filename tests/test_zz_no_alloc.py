@@ -1,4 +1,5 @@
-"""The allocation-free dense gap-current entry point, checked against ion_gj_dense.
+"""The allocation-free dense gap-current entry point, checked against ion_gj_dense (two
+calls in a row) and against the FP64 oracle (up to the largest size its array holds).
 
 ion_gj_dense_noalloc serves callers that cannot allocate device memory (a loop with a
 hard per-step deadline, code inside a stream capture, hosts that own all device memory);
@@ -44,6 +45,25 @@ def test_noalloc_matches_allocating_entry_point_twice(torch_cuda):
         tol = 2e-6 * g * sum_abs_dv(vd) + 1e-30
         assert np.all(np.isfinite(a))
         assert np.all(np.abs(a - b) <= tol), (n, (np.abs(a - b) / tol).max())
+
+
+@pytest.mark.parametrize("n", [1000, 65536])
+def test_noalloc_matches_the_oracle(torch_cuda, O, n):
+    """Against the FP64 oracle (not only the other CUDA entry point), at a small size and at
+    the largest size the fixed array holds (65 536 cells, no padding), same bound as the
+    dense primitive's parity test: 2e-6 * g * sum_j |V_i - V_j|."""
+    torch = torch_cuda
+    vd = (-60.0 + inputs.vdend_jitter(n, 43 + n, 20.0)).astype(np.float32)
+    g = inputs.junction_weight(0.04, n)
+    v = torch.from_numpy(vd).cuda()
+    ic = torch.full((n,), float("nan"), dtype=torch.float32, device="cuda")
+    ion.ion_gj_dense_noalloc(v, g, ic)
+    torch.cuda.synchronize()
+    got = ic.cpu().numpy().astype(np.float64)
+    ref = O.gj_dense(vd.astype(np.float64), g, threads=max(1, O.max_threads()))
+    tol = 2e-6 * g * sum_abs_dv(vd) + 1e-30
+    assert np.all(np.isfinite(got))
+    assert np.all(np.abs(got - ref) <= tol), (n, (np.abs(got - ref) / tol).max())
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(torch_cuda):
