@@ -107,6 +107,9 @@ enum ion_flag {
     ION_FLAG_SGJ = 1u << 8,        /* SGJ use case (Sec. 2.3.2): each connection contributes
                                       w (V_i - V_j) instead of the RGJ term.  Dense or CSR;
                                       not with PERSISTENT, SURROGATE, SPLIT or batches      */
+    ION_FLAG_SURROGATE_WARP_MMA = 1u << 10, /* with SURROGATE: run the MLP on warp-level
+                                      mma.sync (m16n8k16) instead of tcgen05 with TMEM
+                                      accumulators (kept for comparison)                   */
     ION_FLAG_NO_PDL = 1u << 9      /* launch the per-step kernels as ordinary stream-ordered
                                       launches.  By default each is launched with programmatic
                                       stream serialization: its CTAs may be scheduled while the
@@ -241,7 +244,14 @@ ion_status ion_create(const ion_net *net, const ion_conn *conn, const ion_params
  * cell i is global cell offset_b + i, offset_b = n_0 + ... + n_{b-1}); init_state, the
  * state read and written, pulse cells and trace samples all use this numbering.
  * Dense networks may have at most 8192 cells; CSR arrays must be host memory.
- * ION_FLAG_PERSISTENT, ION_FLAG_SPLIT and ION_FLAG_SURROGATE are not supported here. */
+ * ION_FLAG_PERSISTENT: each ion_step call is one cooperative launch (replayed from a CUDA
+ * graph) that advances every network by all its steps.  The networks are cut into pieces
+ * of at most 256 rows, dealt out to CTAs that are all resident at once; a piece waits
+ * (bounded by barrier_timeout_ns, then ION_ERR_TIMEOUT) only until every piece of its own
+ * network has finished the previous step, so there is no grid-wide barrier.  The states
+ * equal those of the per-step launches bit for bit.  Dense evoked input (ION_INPUT_DENSE)
+ * falls back to per-step launches; not with ION_FLAG_CSR_AS_GIVEN.
+ * ION_FLAG_SPLIT, ION_FLAG_SGJ and ION_FLAG_SURROGATE are not supported here. */
 ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, const ion_conn *conns,
                             const ion_params *params, const float *init_state,
                             ion_sim **out);
@@ -394,7 +404,8 @@ ion_status ion_cell_update(float *state, int32_t n, const float *ic, const float
 /* ---- measurement ------------------------------------------------------------------ */
 
 /* Throughput probe of one execution unit at the current clock: what = 0 measures SFU
- * ex2.approx results per second, what = 1 FP32 FMAs per second, over the whole GPU
+ * ex2.approx results per second, what = 1 FP32 FMAs per second, what = 2 tanh.approx.bf16x2
+ * instructions per second (two activations each), over the whole GPU
  * (8 independent chains per thread, 8 CTAs of 256 threads per SM, `iters` rounds).
  * These are the measured denominators of the dense gap-junction kernel's roofline.
  * Synchronises the stream.  Not part of the paper's method. */

@@ -388,6 +388,8 @@ void ion_sim_free_device(ion_sim *s) {
     s->d_cellp = nullptr;
     cudaFree(s->d_mid);
     cudaFree(s->d_mlp);
+    cudaFree(s->d_mlp_tc);
+    s->d_mlp_tc = nullptr;
     s->extra_free(s);
 }
 

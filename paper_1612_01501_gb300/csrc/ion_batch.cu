@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
         }
         uint32_t uses[2] = {0u, 0u};
         float tot[R], Us, Uc;
-        if (!gj_pass<R, 1>(sm, net_v, T.n, T.n_pad, bar, uses, m_shift, ui, 0, lane, a.kahan, tot, Us, Uc)) {
+        if (!gj_pass<R, 1>(sm, net_v, T.n, T.n_pad, bar, uses, m_shift, ui, 0, lane, a.kahan, warp == 0, tot, Us, Uc)) {
             if (threadIdx.x == 0) {
                 atomicOr(c.status, (uint32_t)ST_TIMEOUT);
                 (void)mbar_wait_bounded(&bar[0], uses[0] & 1u);
@@ -229,6 +229,214 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
     finish_cell(c, t, vnext, i, o);
 }
 
+// ---- persistent form: many steps of every network in one cooperative launch -------------
+// The host cuts every network into pieces of at most 256 rows (one piece for a network
+// whose work fits a CTA's share of a step, several for the large ones) and deals the
+// pieces out to CTAs that are all resident at once.  Each CTA walks its pieces once per
+// step.  Before reading network b's V_dend(t) it waits (bounded) until every piece of b
+// has finished step t - 1: each piece adds 1 to b's arrival counter when its rows' states
+// and V_dend(t + 1) are written, so b is ready for step k of the launch once its counter
+// holds k x (pieces of b).  No CTA ever waits on a later step than its own, so the CTA
+// with the oldest step always progresses: the launch cannot deadlock, and no grid-wide
+// barrier is needed.  The pair loop, the CSR row sums and the cell update are those of
+// the per-step kernel (the same lanes per row and rows per warp give the same sums), so
+// the states equal those of the per-step launches bit for bit.
+struct PersistItem {
+    int32_t kind;     // TILE_DENSE or TILE_CSR
+    int32_t net;      // network (index of its arrival counter)
+    int32_t seg, n, n_pad;
+    int32_t row0;     // first row (padded cell index)
+    int32_t rows;     // 1..256
+    int32_t pieces;   // pieces of this network (arrivals per step)
+    int32_t sw;       // CSR: lanes per row
+    int32_t mode;     // CSR: TileMode bits
+    float g;
+};
+
+struct BatchPersistArgs {
+    StepCommon c;              // par = -1; the launch runs steps *t_dev .. *t_dev + n_steps - 1
+    const PersistItem *items;  // every CTA's pieces, CTA after CTA
+    const int32_t *cta_off;    // [gridDim.x + 1] first piece of each CTA
+    const int32_t *row_ptr;
+    const uint16_t *col16;
+    const float *w;
+    uint32_t *cnt;             // arrival counter per network (zeroed before the launch)
+    uint32_t *abort_flag;      // set by a CTA whose wait gave up (zeroed before the launch)
+    uint64_t timeout_ns;
+    int32_t n_steps;
+    int32_t vbuf;              // floats of the staged V_dend buffer (>= n_pad of staged networks)
+    int32_t kahan;
+    int64_t debug_delay_ns;    // test hook: CTA 0 sleeps this long before its first piece
+};
+
+// Bounded wait until *cnt has reached target (mod 2^32), by one thread.  On timeout sets
+// the timeout status bit and the abort word; returns false on timeout or abort.
+__device__ __forceinline__ bool wait_arrivals(const uint32_t *cnt, uint32_t target, uint32_t *abort_flag,
+                                              uint64_t timeout_ns, uint32_t *status) {
+    if (arrivals_reached(ld_acquire_gpu(cnt), target)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (arrivals_reached(ld_acquire_gpu(cnt), target)) return true;
+        if ((it & 63u) == 0u) {
+            if (ld_acquire_gpu(abort_flag) != 0u) return false;
+            if (globaltimer_ns() - t0 > timeout_ns || it > (1u << 30)) {
+                atomicOr(status, (uint32_t)ST_TIMEOUT);
+                atomicExch(abort_flag, 1u);
+                return false;
+            }
+        }
+    }
+}
+
+// Rows [row0, row0 + rows) of a CSR piece with 16-bit local columns: SW lanes per row,
+// row voltages from vrow(local row), neighbour voltages from vj.
+template <int SW, bool HAS_W, class VR, class VJ>
+__device__ __forceinline__ void persist_csr_rows(const BatchPersistArgs &a, const PersistItem &P, VR vrow, VJ vj,
+                                                 float *ic_s) {
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    for (int rr = sub; rr - sub < P.rows; rr += nsub) {   // the same trip count in every lane
+        float acc = 0.0f;
+        if (rr < P.rows) {
+            const int i = P.row0 + rr;
+            const int e0 = a.row_ptr[i], e1 = a.row_ptr[i + 1];
+            if (e1 > e0) acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, e0, e1, vrow(i - P.seg), li, vj);
+        }
+#pragma unroll
+        for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (li == 0 && rr < P.rows) ic_s[rr] = (HAS_W ? acc : acc * P.g) * (1.0f / GJ_SCALE);
+    }
+}
+template <class VR, class VJ>
+__device__ __forceinline__ void persist_csr_piece(const BatchPersistArgs &a, const PersistItem &P, VR vrow, VJ vj,
+                                                  float *ic_s) {
+#define ION_CSR_SW(SWV)                                                                    \
+    if (P.mode & TILE_UNIFORM_W) persist_csr_rows<SWV, false>(a, P, vrow, vj, ic_s);       \
+    else persist_csr_rows<SWV, true>(a, P, vrow, vj, ic_s);
+    switch (P.sw) {
+        case 1: ION_CSR_SW(1) break;
+        case 2: ION_CSR_SW(2) break;
+        case 4: ION_CSR_SW(4) break;
+        case 8: ION_CSR_SW(8) break;
+        case 16: ION_CSR_SW(16) break;
+        default: ION_CSR_SW(32) break;
+    }
+#undef ION_CSR_SW
+}
+
+struct VRowSmem {
+    const float *v;
+    __device__ __forceinline__ float operator()(int j) const { return v[j]; }
+};
+struct VRowCG {
+    const float *v;
+    __device__ __forceinline__ float operator()(int j) const { return __ldcg(v + j); }
+};
+
+// 256 threads: 8 warps; dense pieces run 8 x R rows at a time.
+template <int R>
+__global__ void __launch_bounds__(256, 4) batch_persist_kernel(const BatchPersistArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float red_s[32], red_c[32];
+    __shared__ float U_sh;
+    __shared__ float ic_s[256];
+    __shared__ int ok_sh;
+    float *vb = reinterpret_cast<float *>(smem_raw);   // the piece's network's V_dend(t)
+    float *part = vb + a.vbuf;                          // 8 R row partials
+    const StepCommon &c = a.c;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it0 = a.cta_off[blockIdx.x], it1 = a.cta_off[blockIdx.x + 1];
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const int64_t t0 = *c.t_dev;
+    uint32_t phase = 0;
+    if (a.debug_delay_ns > 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        const uint64_t d0 = globaltimer_ns();
+        while (globaltimer_ns() - d0 < (uint64_t)a.debug_delay_ns) __nanosleep(1000);
+    }
+    for (int k = 0; k < a.n_steps; ++k) {
+        const int64_t t = t0 + k;
+        const float *vcur = vd_slot(c.S, t);
+        float *vnext = vd_slot(c.S, t + 1);
+        for (int it = it0; it < it1; ++it) {
+            const PersistItem P = a.items[it];
+            const bool staged = P.kind == TILE_DENSE || (P.mode & TILE_STAGE_V);
+            if (threadIdx.x == 0) {
+                // network P.net finished step t - 1 (the launch's own earlier steps only)
+                int ok = k == 0 || wait_arrivals(a.cnt + P.net, (uint32_t)k * (uint32_t)P.pieces, a.abort_flag,
+                                                 a.timeout_ns, c.status);
+                if (ok && staged) {
+                    // the acquire above (or stream order) made the writes visible to this
+                    // thread; order them before the bulk copy's async-proxy reads
+                    asm volatile("fence.proxy.async;" ::: "memory");
+                    mbar_expect_tx(&bar, (uint32_t)P.n_pad * 4u);
+                    bulk_g2s(vb, vcur + P.seg, (uint32_t)P.n_pad * 4u, &bar);
+                }
+                ok_sh = ok;
+            }
+            __syncthreads();
+            if (!ok_sh) return;
+            if (staged) {
+                const bool landed = mbar_wait_bounded(&bar, phase & 1u);
+                phase++;
+                if (__syncthreads_or(!landed)) {
+                    if (threadIdx.x == 0) {
+                        atomicOr(c.status, (uint32_t)ST_TIMEOUT);
+                        atomicExch(a.abort_flag, 1u);
+                        (void)mbar_wait_bounded(&bar, (phase - 1u) & 1u);
+                    }
+                    return;
+                }
+            }
+            if (P.kind == TILE_DENSE) {
+                const DenseSmem sm{vb, P.n_pad, 1, part};
+                const float m_shift = vb[0];
+                for (int sub = 0; sub < P.rows; sub += 8 * R) {
+                    const int local0 = P.row0 - P.seg + sub;
+                    const int srows = min(8 * R, P.rows - sub);
+                    float ui[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        ui[r] = (warp * R + r < srows) ? (vb[local0 + warp * R + r] - m_shift) * GJ_SCALE : 0.0f;
+                    uint32_t uses[2] = {0u, 0u};
+                    float tot[R], Us, Uc;
+                    (void)gj_pass<R, 1>(sm, nullptr, P.n, P.n_pad, nullptr, uses, m_shift, ui, 0, lane, a.kahan,
+                                        warp == 0, tot, Us, Uc);
+                    const float U = gj_reduce<R, 1>(sm, tot, Us, Uc, warp, 0, lane, red_s, red_c, &U_sh);
+                    if ((int)threadIdx.x < srows)
+                        ic_s[sub + threadIdx.x] = row_current<1>(sm, threadIdx.x,
+                                                                 (vb[local0 + threadIdx.x] - m_shift) * GJ_SCALE,
+                                                                 P.n, U, P.g);
+                    __syncthreads();   // part[] is rewritten by the next row block
+                }
+            } else if (P.mode & TILE_STAGE_V) {
+                persist_csr_piece(a, P, VRowSmem{vb}, VjShared{vb}, ic_s);
+            } else {
+                persist_csr_piece(a, P, VRowCG{vcur + P.seg}, VjGlobalCG{vcur + P.seg}, ic_s);
+            }
+            __syncthreads();
+            // the explicit-Euler update of the piece's rows, one thread per cell (a thread
+            // reads its cell's step-t words before writing any of them)
+            for (int rr = threadIdx.x; rr < P.rows; rr += blockDim.x) {
+                const int64_t i = P.row0 + rr;
+                const float vd = staged ? vb[i - P.seg] : __ldcg(vcur + i);
+                float iapp = pulse_current(c.pulses, i, t);
+                if (c.iapp != nullptr) iapp += c.iapp[i];
+                const CellNext o = cell_step(c.P, load_cell(c.S, vcur, i, vd), ic_s[rr], iapp);
+                finish_cell(c, t, vnext, i, o);
+            }
+            // every thread's reads of vb come before the next piece's bulk refill of it
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            // the CTA's writes (ordered before the barrier above) precede the arrival
+            if (threadIdx.x == 0) red_release_gpu_add(a.cnt + P.net, 1u);
+        }
+    }
+}
+
 // gather / scatter between the user's numbering (consecutive cells) and the segments
 __global__ void batch_gather_kernel(const float *state, int64_t stride, const int32_t *map, int64_t n_user,
                                     int32_t vd_slot_field, float *out) {
@@ -267,6 +475,17 @@ struct BatchNet {
 
 struct BatchExt {
     std::vector<BatchNet> nets;
+    // persistent form (ION_FLAG_PERSISTENT): pieces dealt out to the CTAs of one
+    // cooperative launch, per-network arrival counters + the abort word, and the graph of
+    // one launch (counter reset, kernel, step-counter advance) for the last step count
+    bool persistent = false;
+    PersistItem *d_items = nullptr;
+    int32_t *d_cta_off = nullptr;
+    uint32_t *d_pcnt = nullptr;     // n_nets counters, then the abort word
+    int p_grid = 0, p_vbuf = 256, p_pieces = 0;
+    cudaGraphExec_t p_graph = nullptr;
+    int64_t p_graph_steps = 0;
+    bool p_graph_refused = false;
     std::vector<int32_t> h_map;     // user cell -> padded cell
     BatchTile *d_tiles = nullptr;
     int n_tiles = 0;
@@ -365,6 +584,225 @@ static cudaError_t batch_step(ion_sim *s, int k_off, const float *iapp) {
     return batch_launch(a, X->R, X->n_tiles, batch_smem(X), s->st, false);
 }
 
+// ---- persistent form: planning and launch ----------------------------------------------
+template <int R>
+static cudaError_t persist_kernel_attr(size_t smem, int *per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(batch_persist_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_persist_kernel<R>, 256, smem);
+    return e;
+}
+static cudaError_t persist_attr(int R, size_t smem, int *per_sm) {
+    switch (R) {
+        case 1: return persist_kernel_attr<1>(smem, per_sm);
+        case 2: return persist_kernel_attr<2>(smem, per_sm);
+        case 4: return persist_kernel_attr<4>(smem, per_sm);
+        default: return cudaErrorInvalidValue;
+    }
+}
+static const void *persist_fn(int R) {
+    switch (R) {
+        case 1: return (const void *)batch_persist_kernel<1>;
+        case 2: return (const void *)batch_persist_kernel<2>;
+        default: return (const void *)batch_persist_kernel<4>;
+    }
+}
+static size_t persist_smem(const BatchExt *X) { return (size_t)X->p_vbuf * 4 + 8 * X->R * 4; }
+
+// Cut the networks into pieces and deal them out to the CTAs of one resident grid.
+// Work per row: a dense row costs its network's padded width in pair evaluations (plus a
+// constant for its update), a CSR row 3 units per edge and 60 for its update; a piece
+// also pays its staging.  A network becomes several pieces when its work exceeds a CTA's
+// share of the total (and pieces hold at most 256 rows); pieces go largest first to the
+// least loaded CTA.  Each CTA handles the pieces of networks split over several CTAs
+// first, so that their arrivals come early in every step.
+static ion_status batch_persist_plan(ion_sim *s) {
+    BatchExt *X = ext_of(s);
+    if (X->R != 1 && X->R != 2 && X->R != 4) X->R = 2;
+    X->p_vbuf = X->max_dense_pad;
+    int per_sm = 0;
+    cudaError_t e = persist_attr(X->R, persist_smem(X), &per_sm);
+    if (e != cudaSuccess || per_sm < 1)
+        return ion_fail(s, ION_ERR_UNSUPPORTED, "persistent batch: no resident CTA (%s)", cudaGetErrorString(e));
+    const int grid = per_sm * s->sms;
+    struct Net { double per_row, fixed; int rows_align; };
+    std::vector<Net> nc(X->nets.size());
+    double total = 0.0;
+    for (size_t b = 0; b < X->nets.size(); ++b) {
+        const BatchNet &x = X->nets[b];
+        if (x.kind == ION_DENSE_UNIFORM) nc[b] = {(double)x.n_pad + 64.0, 2048.0 + x.n_pad, 8 * X->R};
+        else nc[b] = {3.0 * (x.n > 0 ? (double)x.nnz / x.n : 0.0) + 60.0, 2048.0 + 0.5 * x.n_pad, 32};
+        total += nc[b].per_row * x.n + nc[b].fixed;
+    }
+    const double share = total / grid;
+    struct Piece { PersistItem it; double cost; };
+    std::vector<Piece> pieces;
+    for (size_t b = 0; b < X->nets.size(); ++b) {
+        const BatchNet &x = X->nets[b];
+        const double cost = nc[b].per_row * x.n;
+        int k = std::max((x.n + 255) / 256, (int)std::ceil(cost / (0.8 * share)));
+        k = std::max(1, std::min(k, x.n));
+        int rows = (x.n + k - 1) / k;
+        const int al = nc[b].rows_align;
+        rows = std::min(256, (rows + al - 1) / al * al);
+        k = (x.n + rows - 1) / rows;
+        for (int r = 0; r < x.n; r += rows) {
+            PersistItem it{};
+            it.kind = x.kind == ION_DENSE_UNIFORM ? TILE_DENSE : TILE_CSR;
+            it.net = (int32_t)b;
+            it.seg = x.seg;
+            it.n = x.n;
+            it.n_pad = x.n_pad;
+            it.row0 = x.seg + r;
+            it.rows = std::min(rows, x.n - r);
+            it.pieces = k;
+            it.g = x.g;
+            if (x.kind != ION_DENSE_UNIFORM) {
+                it.sw = x.sw;
+                it.mode = (x.uniform ? TILE_UNIFORM_W : 0) | (x.c16 ? TILE_C16 : 0);
+                if (x.c16 && x.n_pad <= X->p_vbuf) it.mode |= TILE_STAGE_V;
+            }
+            pieces.push_back({it, nc[b].per_row * it.rows + nc[b].fixed});
+        }
+    }
+    std::vector<int> order(pieces.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return pieces[a].cost > pieces[b].cost; });
+    std::vector<double> load((size_t)grid, 0.0);
+    std::vector<std::vector<int>> own((size_t)grid);
+    for (int q : order) {
+        const size_t c = (size_t)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[c] += pieces[q].cost;
+        own[c].push_back(q);
+    }
+    std::vector<PersistItem> items;
+    std::vector<int32_t> off((size_t)grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        std::vector<int> &L = own[(size_t)c];
+        std::stable_sort(L.begin(), L.end(), [&](int a, int b) {
+            const PersistItem &A = pieces[a].it, &B = pieces[b].it;
+            if ((A.pieces > 1) != (B.pieces > 1)) return A.pieces > 1;
+            return A.row0 < B.row0;
+        });
+        for (int q : L) items.push_back(pieces[q].it);
+        off[(size_t)c + 1] = (int32_t)items.size();
+    }
+    e = cudaStreamSynchronize(s->st);
+    if (X->p_graph) {
+        cudaGraphExecDestroy(X->p_graph);
+        X->p_graph = nullptr;
+        X->p_graph_steps = 0;
+    }
+    cudaFree(X->d_items);
+    cudaFree(X->d_cta_off);
+    X->d_items = nullptr;
+    X->d_cta_off = nullptr;
+    X->p_grid = 0;
+    if (e == cudaSuccess) e = ion_alloc(&X->d_items, std::max<size_t>(1, items.size()) * sizeof(PersistItem));
+    if (e == cudaSuccess) e = ion_alloc(&X->d_cta_off, off.size() * sizeof(int32_t));
+    if (e == cudaSuccess && !X->d_pcnt) e = ion_alloc(&X->d_pcnt, (X->nets.size() + 1) * sizeof(uint32_t));
+    if (e == cudaSuccess && !items.empty())
+        e = cudaMemcpy(X->d_items, items.data(), items.size() * sizeof(PersistItem), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(X->d_cta_off, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return ion_fail(s, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "persistent batch plan: %s",
+                        cudaGetErrorString(e));
+    X->p_grid = grid;
+    X->p_pieces = (int)items.size();
+    return ION_OK;
+}
+
+// One launch of n_steps steps: counters and abort word cleared, the cooperative kernel,
+// then the device step counter advanced.
+static cudaError_t persist_enqueue(ion_sim *s, int n_steps, bool capture) {
+    BatchExt *X = ext_of(s);
+    BatchPersistArgs a{};
+    a.c = ion_step_common(s, 0, nullptr);
+    a.c.par = -1;   // many steps per launch: the slots follow the device counter
+    a.items = X->d_items;
+    a.cta_off = X->d_cta_off;
+    a.row_ptr = s->d_rowptr;
+    a.col16 = s->d_col16;
+    a.w = s->d_w;
+    a.cnt = X->d_pcnt;
+    a.abort_flag = X->d_pcnt + X->nets.size();
+    a.timeout_ns = s->barrier_timeout_ns;
+    a.n_steps = n_steps;
+    a.vbuf = X->p_vbuf;
+    a.kahan = 1;
+    a.debug_delay_ns = s->debug_delay_ns;
+    cudaError_t e = cudaMemsetAsync(X->d_pcnt, 0, (X->nets.size() + 1) * sizeof(uint32_t), s->st);
+    if (e != cudaSuccess) return e;
+    void *args[] = {&a};
+    if (capture) {
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeCooperative;
+        at[0].val.cooperative = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(X->p_grid);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = persist_smem(X);
+        cfg.stream = s->st;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelExC(&cfg, persist_fn(X->R), args);
+    } else {
+        e = cudaLaunchCooperativeKernel(persist_fn(X->R), dim3(X->p_grid), dim3(256), args, persist_smem(X), s->st);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_advance(s->d_t, n_steps, s->st);
+}
+
+// The captured launch holds the pulse table and trace ring of its capture: dropped with
+// the per-step graphs whenever those change.
+static void batch_persist_drop(ion_sim *s) {
+    BatchExt *X = ext_of(s);
+    if (X && X->p_graph) {
+        cudaGraphExecDestroy(X->p_graph);
+        X->p_graph = nullptr;
+        X->p_graph_steps = 0;
+    }
+}
+
+// ion_step of a persistent batch: one graph replay (or, where a capture is refused, one
+// direct cooperative launch) per 2^22 steps.
+static ion_status batch_persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
+    (void)iapp;
+    BatchExt *X = ext_of(s);
+    if (X->d_items == nullptr || X->p_grid == 0) return ion_fail(s, ION_ERR_CUDA, "persistent batch: no plan");
+    int64_t done = 0;
+    while (done < n_steps) {
+        const int chunk = (int)std::min<int64_t>(n_steps - done, 1 << 22);
+        cudaError_t e = cudaSuccess;
+        if (!X->p_graph_refused && X->p_graph_steps != chunk) {
+            if (X->p_graph) cudaGraphExecDestroy(X->p_graph);
+            X->p_graph = nullptr;
+            X->p_graph_steps = 0;
+            cudaGraph_t g = nullptr;
+            e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                const cudaError_t e1 = persist_enqueue(s, chunk, true);
+                const cudaError_t e2 = cudaStreamEndCapture(s->st, &g);
+                e = e1 != cudaSuccess ? e1 : e2;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&X->p_graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (e == cudaSuccess) {
+                X->p_graph_steps = chunk;
+            } else {   // no cooperative launches in graphs here: launch directly from now on
+                (void)cudaGetLastError();
+                X->p_graph = nullptr;
+                X->p_graph_refused = true;
+            }
+        }
+        if (X->p_graph != nullptr && X->p_graph_steps == chunk) e = cudaGraphLaunch(X->p_graph, s->st);
+        else e = persist_enqueue(s, chunk, false);
+        s->launches += 2;
+        if (e != cudaSuccess) return ion_fail(s, ION_ERR_CUDA, "persistent batch launch: %s", cudaGetErrorString(e));
+        done += chunk;
+    }
+    return ION_OK;
+}
+
 static ion_status batch_prepare(ion_sim *s) {
     BatchExt *X = ext_of(s);
     cudaError_t e = batch_launch(BatchArgs{}, X->R, 0, batch_smem(X), s->st, true);
@@ -425,6 +863,11 @@ int32_t ion_batch_map_cell(ion_sim *s, int64_t user_cell) {
 static void batch_free(ion_sim *s) {
     BatchExt *X = ext_of(s);
     if (!X) return;
+    s->drop_hook = nullptr;
+    if (X->p_graph) cudaGraphExecDestroy(X->p_graph);
+    cudaFree(X->d_items);
+    cudaFree(X->d_cta_off);
+    cudaFree(X->d_pcnt);
     cudaFree(X->d_tiles);
     cudaFree(X->d_tmp);
     cudaFree(s->d_map);
@@ -439,8 +882,10 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     *out = nullptr;
     if (n_nets < 1 || !nets || !conns || !params)
         return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_create_batch: bad arguments");
-    if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_PERSISTENT | ION_FLAG_SPLIT | ION_FLAG_SGJ))
+    if (params->flags & (ION_FLAG_SURROGATE | ION_FLAG_SPLIT | ION_FLAG_SGJ))
         return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: flags not supported for batches");
+    if ((params->flags & ION_FLAG_PERSISTENT) && (params->flags & ION_FLAG_CSR_AS_GIVEN))
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: a persistent batch needs the compact CSR layout");
     if (params->cell_params)
         return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: per-cell constants not supported for batches");
     // validate and lay out
@@ -579,6 +1024,17 @@ extern "C" ion_status ion_create_batch(int32_t n_nets, const ion_net *nets, cons
     st = batch_plan(s);
     if (st == ION_OK) st = batch_prepare(s);
     if (st != ION_OK) return fail(st);
+    if (params->flags & ION_FLAG_PERSISTENT) {
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
+        if (!coop) return fail(ion_fail(nullptr, ION_ERR_UNSUPPORTED, "ion_create_batch: no cooperative launches"));
+        X->persistent = true;
+        s->flags |= ION_FLAG_PERSISTENT;
+        st = batch_persist_plan(s);
+        if (st != ION_OK) return fail(st);
+        s->run_override = batch_persist_run;
+        s->drop_hook = batch_persist_drop;
+    }
     *out = s;
     return ION_OK;
 }
@@ -608,8 +1064,11 @@ static ion_status time_steps(ion_sim *s, int steps, float *ms) {
     return ION_OK;
 }
 
+static ion_status autotune_persist_batch(ion_sim *s, int32_t steps, ion_tune *chosen);
+
 extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) {
     if (!s || steps < 1) return ion_fail(s, ION_ERR_INVALID_ARG, "ion_autotune: bad arguments");
+    if (s->ext && s->run_override == batch_persist_run) return autotune_persist_batch(s, steps, chosen);
     if (s->run_override) return ion_fail(s, ION_ERR_UNSUPPORTED, "ion_autotune: persistent handles are not tuned");
     // save the state and the step counter
     float *save = nullptr;
@@ -779,5 +1238,67 @@ extern "C" ion_status ion_autotune(ion_sim *s, int32_t steps, ion_tune *chosen) 
     cudaFree(save);
     if (st != ION_OK) return st;
     if (chosen) *chosen = bt;
+    return ION_OK;
+}
+
+// Persistent batches: rows per warp of the dense pieces (1, 2 or 4), each timed over
+// `steps` steps of one launch, the state and step count restored after each.
+static ion_status autotune_persist_batch(ion_sim *s, int32_t steps, ion_tune *chosen) {
+    BatchExt *X = ext_of(s);
+    float *save = nullptr;
+    const size_t bytes = (size_t)20 * s->stride * sizeof(float);
+    cudaError_t e = cudaStreamSynchronize(s->st);
+    if (e == cudaSuccess) e = ion_alloc(&save, bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(save, s->d_state, bytes, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(save);
+        return ion_fail(s, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_autotune: %s",
+                        cudaGetErrorString(e));
+    }
+    const int64_t t0 = s->t;
+    float best = 1e30f;
+    int bR = X->R;
+    ion_status st = ION_OK;
+    for (int R : {1, 2, 4}) {
+        X->R = R;
+        st = batch_persist_plan(s);
+        if (st != ION_OK) break;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, s->st);
+        st = batch_persist_run(s, steps, nullptr);
+        cudaEventRecord(b, s->st);
+        float ms = 0.0f;
+        e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaMemcpy(s->d_state, save, bytes, cudaMemcpyDeviceToDevice);
+        cudaMemcpy(s->d_t, &t0, sizeof t0, cudaMemcpyHostToDevice);
+        s->t = t0;
+        if (st != ION_OK) break;
+        if (e != cudaSuccess) {
+            st = ion_fail(s, ION_ERR_CUDA, "ion_autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        if (ms < best) {
+            best = ms;
+            bR = R;
+        }
+    }
+    X->R = bR;
+    if (st == ION_OK) st = batch_persist_plan(s);
+    if (st == ION_OK) st = batch_prepare(s);   // the per-step kernel (dense inputs) uses R too
+    if (st == ION_OK) st = batch_plan(s);
+    cudaFree(save);
+    if (st != ION_OK) return st;
+    if (chosen) {
+        *chosen = ion_tune{};
+        chosen->dense_rows_per_warp = bR;
+        chosen->dense_warps = 8;
+        chosen->dense_col_splits = 1;
+        chosen->csr_rows_per_cta = X->csr_rows;
+    }
     return ION_OK;
 }

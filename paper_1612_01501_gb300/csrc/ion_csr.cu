@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             if (e1 > e0) {   // rows past the end (and empty segments) have e0 == e1
                 if (C16)
                     acc = csr_row_sum16<SW, HAS_W, true>(a.col16, a.w, e0, e1, vi, li,
-                                                         VjChunk{vs, (uint32_t)c0 & 0xFFFFu});
+                                                         VjChunk{vs});
                 else
                     acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vi, li);
             }

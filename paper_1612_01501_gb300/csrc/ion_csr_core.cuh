@@ -70,13 +70,30 @@ __device__ __forceinline__ float csr_row_sum_smem(const float *vs, int c0, const
     return acc;
 }
 
-// Eight edges of a 16-byte group of 16-bit columns (and their weights).
+// Two edges of row i at once through packed f32x2 arithmetic (the same terms as gj_edge):
+// dV = V_i - V_j (an FFMA2 with -1: the same bits as a subtraction), du = dV s, then
+// acc += w (0.8 2^{-du^2} + 0.2) du, the last product fused into the accumulation.
+template <bool HAS_W>
+__device__ __forceinline__ float2 gj_edge2(float2 vi2, float2 vj2, float2 w2, float2 acc) {
+    const float2 d = __ffma2_rn(vj2, make_float2(-1.0f, -1.0f), vi2);
+    const float2 du = __fmul2_rn(d, make_float2(GJ_SCALE, GJ_SCALE));
+    const float2 q = __fmul2_rn(du, du);
+    const float2 e = make_float2(ex2_approx(-q.x), ex2_approx(-q.y));
+    float2 f = __ffma2_rn(e, make_float2(0.8f, 0.8f), make_float2(0.2f, 0.2f));
+    if (HAS_W) f = __fmul2_rn(f, w2);
+    return __ffma2_rn(f, du, acc);
+}
+
+// Eight edges of a 16-byte group of 16-bit columns (and their weights), two at a time.
 template <bool HAS_W, class VJ>
 __device__ __forceinline__ float csr_group16(uint4 q, float4 wa, float4 wb, float vi, VJ vj) {
-    const float v0 = vj(q.x & 0xFFFFu), v1 = vj(q.x >> 16), v2 = vj(q.y & 0xFFFFu), v3 = vj(q.y >> 16);
-    const float v4 = vj(q.z & 0xFFFFu), v5 = vj(q.z >> 16), v6 = vj(q.w & 0xFFFFu), v7 = vj(q.w >> 16);
-    return ((gj_edge(vi, v0, wa.x) + gj_edge(vi, v1, wa.y)) + (gj_edge(vi, v2, wa.z) + gj_edge(vi, v3, wa.w))) +
-           ((gj_edge(vi, v4, wb.x) + gj_edge(vi, v5, wb.y)) + (gj_edge(vi, v6, wb.z) + gj_edge(vi, v7, wb.w)));
+    const float2 vi2 = make_float2(vi, vi);
+    float2 acc = make_float2(0.0f, 0.0f);
+    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.x & 0xFFFFu), vj(q.x >> 16)), make_float2(wa.x, wa.y), acc);
+    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.y & 0xFFFFu), vj(q.y >> 16)), make_float2(wa.z, wa.w), acc);
+    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.z & 0xFFFFu), vj(q.z >> 16)), make_float2(wb.x, wb.y), acc);
+    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.w & 0xFFFFu), vj(q.w >> 16)), make_float2(wb.z, wb.w), acc);
+    return acc.x + acc.y;
 }
 template <bool HAS_W, bool LD_STREAM>
 __device__ __forceinline__ void csr_load16(const uint16_t *__restrict__ col16, const float *__restrict__ w, int e,
@@ -129,6 +146,18 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
     } else {
         for (int eh = e0 + li; eh < ea; eh += SW) acc += gj_edge(vi, vj(csr_ld16<LD_STREAM>(col16, eh)), HAS_W ? __ldg(w + eh) : 1.0f);
     }
+    if (!HAS_W) {   // long rows: four groups (64 B of indices per lane) in flight per round
+        for (; e + 24 * SW < eb; e += 32 * SW) {
+            uint4 q0, q1, q2, q3;
+            float4 u0, u1;
+            csr_load16<false, LD_STREAM>(col16, w, e, q0, u0, u1);
+            csr_load16<false, LD_STREAM>(col16, w, e + 8 * SW, q1, u0, u1);
+            csr_load16<false, LD_STREAM>(col16, w, e + 16 * SW, q2, u0, u1);
+            csr_load16<false, LD_STREAM>(col16, w, e + 24 * SW, q3, u0, u1);
+            acc += (csr_group16<false>(q0, u0, u1, vi, vj) + csr_group16<false>(q1, u0, u1, vi, vj)) +
+                   (csr_group16<false>(q2, u0, u1, vi, vj) + csr_group16<false>(q3, u0, u1, vi, vj));
+        }
+    }
     for (; e + 8 * SW < eb; e += 16 * SW) {                 // further rounds: two groups in flight
         uint4 q0, q1;
         float4 a0, b0, a1, b1;
@@ -152,12 +181,19 @@ struct VjGlobal {
     const float *v;
     __device__ __forceinline__ float operator()(uint32_t j) const { return __ldg(v + j); }
 };
+// The same through L2 only (ld.global.cg): for data other CTAs of a persistent launch wrote
+// earlier in the same launch, which the non-coherent read-only and L1 paths may hold stale
+struct VjGlobalCG {
+    const float *v;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return __ldcg(v + j); }
+};
 // V_dend of a column of the shared-memory chunk starting at c0 (a multiple of 32 768):
-// the column is c0 + ((j - c0) mod 2^16) and lies in the chunk, so the low 16 bits suffice
+// the column lies in [c0, c0 + 32 768), so its low 15 bits are its offset in the chunk
+// (j holds the column's low 16 bits, possibly with other bits above them)
+static_assert(CSR_CHUNK == 32768, "chunk-relative columns are the low 15 bits");
 struct VjChunk {
     const float *vs;
-    uint32_t c0lo;   // c0 mod 2^16
-    __device__ __forceinline__ float operator()(uint32_t j) const { return vs[(j - c0lo) & 0xFFFFu]; }
+    __device__ __forceinline__ float operator()(uint32_t j) const { return vs[j & 0x7FFFu]; }
 };
 
 }  // namespace ion

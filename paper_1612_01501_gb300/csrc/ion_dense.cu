@@ -12,15 +12,20 @@
 //
 // Layout (N-body style): V_dend(t) is staged into shared memory in tiles of TJ floats by
 // 1-D bulk async copies (cp.async.bulk, completion on an mbarrier), double-buffered when
-// N > TJ, then centred, scaled and negated in place (the tile holds -u_j).  A CTA has
-// GR x GJ warps: GR row groups of R rows and GJ interleaved column splits.  Each lane
-// holds u_i of its R rows and walks its columns four at a time (one 16-byte shared load
-// feeds 4 x R pairs); pairs go two at a time through packed f32x2 arithmetic (per two
-// pairs: one FADD2, one FMUL2, two ex2, one FFMA2).  Lane sums are folded into Kahan-
-// compensated accumulators every 64 columns, then summed pairwise across lanes (a fixed
-// butterfly) and across column splits, so results are deterministic.  The fused step
-// then runs the explicit-Euler cell update of the CTA's rows (one thread per row) and
-// writes V_dend(t+1) to the other V_dend buffer.
+// N > TJ.  A CTA has GR x GJ warps: GR row groups of R rows and GJ interleaved column
+// splits.  Each lane holds u_i of its R rows and walks its columns four at a time: one
+// 16-byte shared load of raw V_dend, centred, scaled and negated in registers
+// (x_j = -(V_j - m) s: two packed f32x2 operations per four columns), then 4 x R pairs
+// through packed f32x2 arithmetic (per two pairs: one FADD2, one FMUL2, two ex2, one
+// FFMA2).  The warps of the first row group also sum the x_j of the real columns (the
+// linear part's sum_j u_j).  Lane sums are folded into Kahan-compensated accumulators
+// every 64 columns, then summed pairwise across lanes (a fixed butterfly) and across
+// column splits, so results are deterministic.
+//
+// The fused step then runs the explicit-Euler cell update of the CTA's rows, spread over
+// NROLE threads per cell (the dendrite, the soma and axon voltages, and groups of gates:
+// see cell_step_role), from the rows' state words that cp.async copied into shared memory
+// while the pair loop ran; it writes V_dend(t+1) to the other V_dend buffer.
 //
 // Per-step launches are programmatically dependent (launch_k, pdl_enter): the kernel may
 // be scheduled while the previous step drains, initialises its mbarriers, then waits for
@@ -53,7 +58,7 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     const int W = blockDim.x >> 5;
     const int GR = W / GJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rg = warp % GR, cs = warp / GR;
+    const int rg = warp % GR, csp = warp / GR;
     const int rows_cta = GR * R;
     const DenseSmem sm = dense_smem(smem_raw, c.n_pad);
     if (threadIdx.x == 0) {
@@ -67,9 +72,13 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     const float *vcur = a.vd_in != nullptr ? a.vd_in : vd_cur(c);
     float *vnext = a.fuse ? vd_next(c) : nullptr;
     const int row_base = blockIdx.x * rows_cta;
+    float *cs = sm.part + W * R;              // staged Cell words of the CTA's rows
+    float *ic_s = cs + NCW * rows_cta;        // their gap currents
     __syncthreads();
     if (threadIdx.x == 0)
         for (int k = 0; k < 2 && k < sm.n_tiles; ++k) issue_tile(sm, vcur, c.n_pad, k, bar);
+    // the rows' state words travel to shared memory while the pair loop runs
+    if (a.fuse) stage_cells(cs, c.S, vcur, row_base, rows_cta, n);
     const float m_shift = vcur[0];
 
     float ui[R];
@@ -80,7 +89,7 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
     }
     uint32_t uses[2] = {0u, 0u};
     float tot[R], Us, Uc;
-    if (!gj_pass<R, GJ>(sm, vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan, tot, Us, Uc)) {
+    if (!gj_pass<R, GJ>(sm, vcur, n, c.n_pad, bar, uses, m_shift, ui, csp, lane, a.kahan, rg == 0, tot, Us, Uc)) {
         if (threadIdx.x == 0) {
             if (c.status != nullptr) atomicOr(c.status, (uint32_t)ST_TIMEOUT);   // primitives pass none
             // let any copy still in flight land before the CTA's shared memory is released
@@ -90,23 +99,33 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
         if (!a.fuse)
             for (int rr = threadIdx.x; rr < rows_cta && row_base + rr < n; rr += blockDim.x)
                 a.ic_out[row_base + rr] = __int_as_float(0x7fc00000);
+        cp_async_wait_all();   // no staging copy may still be landing when the CTA exits
         return;
     }
-    const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, cs, lane, red_s, red_c, &U_sh);
+    const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, csp, lane, red_s, red_c, &U_sh);
 
     for (int rr = threadIdx.x; rr < rows_cta; rr += blockDim.x) {
         const int i = row_base + rr;
         if (i >= n) break;
         const float ic = row_current<GJ>(sm, rr, (vcur[i] - m_shift) * GJ_SCALE, n, U, a.g);
-        if (!a.fuse) {
-            a.ic_out[i] = ic;
-            continue;
+        if (!a.fuse) a.ic_out[i] = ic;
+        else ic_s[rr] = ic;
+    }
+    if (!a.fuse) return;
+    cp_async_wait_all();
+    __syncthreads();
+    // each cell's outputs spread over NROLE threads (a warp holds one role of 32 rows)
+    const int rows32 = (rows_cta + 31) & ~31;
+    for (int q = threadIdx.x; q < NROLE * rows32; q += blockDim.x) {
+        const int role = q / rows32, rr = q - role * rows32;
+        const int i = row_base + rr;
+        if (rr >= rows_cta || i >= n) continue;
+        float iapp = 0.0f;
+        if (role == 0) {
+            iapp = pulse_current(c.pulses, i, t);
+            if (c.iapp != nullptr) iapp += c.iapp[i];
         }
-        const Cell cell = load_cell(c.S, vcur, i);
-        float iapp = pulse_current(c.pulses, i, t);
-        if (c.iapp != nullptr) iapp += c.iapp[i];
-        const CellNext o = cell_step(c.P, cell, ic, iapp);
-        finish_cell(c, t, vnext, i, o);
+        cell_step_role(role, c, t, vnext, i, staged_cell(cs, rows_cta, rr), ic_s[rr], iapp);
     }
 }
 
@@ -193,10 +212,9 @@ __global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kerne
             const int i = row_base + rg * R + r;
             ui[r] = (i < n) ? ((single ? sm.tile0[i] : __ldcg(vcur + i)) - m_shift) * GJ_SCALE : 0.0f;
         }
-        __syncthreads();   // the in-place scaling below overwrites the tile the loads above read
         float tot[R], Us, Uc;
-        if (!gj_pass<R, GJ>(sm, single ? nullptr : vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan, tot,
-                            Us, Uc)) {
+        if (!gj_pass<R, GJ>(sm, single ? nullptr : vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan,
+                            rg == 0, tot, Us, Uc)) {
             if (threadIdx.x == 0) {
                 atomicOr(c.status, (uint32_t)ST_TIMEOUT);
                 atomicExch(a.abort_flag, 1u);
@@ -246,6 +264,10 @@ size_t dense_smem_bytes(int n_pad, int R, int W) {
     const size_t tiles = (n_tiles > 1 ? 2 * TJ : n_pad) * sizeof(float);
     return tiles + (size_t)W * R * sizeof(float);   // part[rows_cta][GJ] = (W / GJ) * R * GJ floats
 }
+// the per-step kernel also stages its rows' Cell words and keeps their currents
+static size_t dense_step_smem_bytes(int n_pad, int R, int W, int GJ) {
+    return dense_smem_bytes(n_pad, R, W) + (size_t)(NCW + 1) * (W / GJ) * R * sizeof(float);
+}
 
 // ---- launch-shape dispatch: R rows per warp, W warps = (W / GJ) row groups x GJ splits ----
 template <template <int, int> class Op, int R>
@@ -281,7 +303,7 @@ struct StepOp {
     static cudaError_t run(StepLaunch &L) {
         if (L.W % GJ != 0 || L.W * 32 > DenseBounds<R>::threads) return cudaErrorInvalidValue;
         const int rows_cta = (L.W / GJ) * R;
-        const size_t smem = dense_smem_bytes(L.a->c.n_pad, R, L.W);
+        const size_t smem = dense_step_smem_bytes(L.a->c.n_pad, R, L.W, GJ);
         if (L.prepare_only)
             return cudaFuncSetAttribute(dense_step_kernel<R, GJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         const int grid = (L.a->c.n + rows_cta - 1) / rows_cta;

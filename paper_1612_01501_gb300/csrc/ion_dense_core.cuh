@@ -10,7 +10,7 @@
 
 namespace ion {
 
-constexpr float PAD_U = 1.0e6f;   // |u| of padded columns: 2^{-PAD_U^2} is exactly 0
+constexpr float PAD_U = 1.0e6f;   // |u| of padded columns: 2^{-PAD_U^2} is exactly 0 (matrix kernel)
 
 struct DenseSmem {
     float *tile0;     // buffer b at tile0 + b * buf_len
@@ -35,20 +35,70 @@ __device__ __forceinline__ void issue_tile(const DenseSmem &sm, const float *src
     bulk_g2s(sm.tile0 + (k & 1) * sm.buf_len, src + (int64_t)k * TJ, (uint32_t)len * 4u, &bar[k & 1]);
 }
 
+// One block of the pair loop: BLK float4 columns of one lane (m0, m0 + 32 GJ, ...), every
+// column against the lane's R rows, summed into acc[r]; with SUMU also the column values
+// x_j of the real columns into su.  CHECK: the block may run past n4 (the last block of a
+// tile), so each column is tested; a full block runs without tests.
+template <int R, int GJ, int BLK, bool SUMU, bool CHECK>
+__device__ __forceinline__ void gj_block(const float4 *t4, int m0, int n4, int full4, int real, float2 negm2,
+                                         float2 negs2, const float2 (&u2)[R], float2 (&acc)[R], float2 &su) {
+#pragma unroll 4
+    for (int mm = 0; mm < BLK; ++mm) {
+        const int m = m0 + mm * 32 * GJ;
+        if (CHECK && m >= n4) break;
+        const float4 v = t4[m];
+        const float2 va = __fmul2_rn(__fadd2_rn(make_float2(v.x, v.y), negm2), negs2);
+        const float2 vb = __fmul2_rn(__fadd2_rn(make_float2(v.z, v.w), negm2), negs2);
+        if (SUMU) {
+            if (!CHECK || m < full4) {
+                su = __fadd2_rn(su, va);
+                su = __fadd2_rn(su, vb);
+            } else {   // the one float4 that ends in padding
+                const int rem = real - 4 * m;
+                su.x += va.x;
+                if (rem > 1) su.y += va.y;
+                if (rem > 2) su.x += vb.x;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 da = __fadd2_rn(u2[r], va);
+            const float2 db = __fadd2_rn(u2[r], vb);
+            const float2 qa = __fmul2_rn(da, da);
+            const float2 qb = __fmul2_rn(db, db);
+            const float2 ea = make_float2(ex2_approx(-qa.x), ex2_approx(-qa.y));
+            const float2 eb = make_float2(ex2_approx(-qb.x), ex2_approx(-qb.y));
+            acc[r] = __ffma2_rn(ea, da, acc[r]);
+            acc[r] = __ffma2_rn(eb, db, acc[r]);
+        }
+    }
+}
+
 // One pass over all columns.  If `src` is non-NULL the first two tiles must already be in
 // flight (issue_tile) and the remaining ones are issued here; if NULL the single tile
-// already holds raw V_dend (single-CTA persistent mode).  On return tot[r] holds this
-// lane's compensated column sum for row r, and (Us, Uc) this thread's share of
-// sum_j u_j.  bar_uses counts completed phases of each mbarrier.  Returns false (in
-// every thread) if a bulk copy did not land in time.
+// already holds V_dend (single-CTA persistent mode).  The tiles hold raw V_dend: each lane
+// centres, scales and negates the four columns of a 16-byte load as it reads them,
+// x_j = -(V_j - m) s (the same bits a separate transform pass would store), so there is no
+// pass over the tile between its arrival and the pair loop.  Columns past the last real
+// cell are skipped.  On return tot[r] holds this lane's compensated column sum for row r,
+// and (Us, Uc) this thread's compensated share of sum_j u_j if sum_u (warps of one row
+// group together cover every column once), else zero.  bar_uses counts completed phases
+// of each mbarrier.  Returns false (in every thread) if a bulk copy did not land in time.
 template <int R, int GJ>
 __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, int n, int n_pad, uint64_t *bar,
                                         uint32_t (&bar_uses)[2], float m_shift, const float (&ui)[R], int cs,
-                                        int lane, int kahan, float (&tot)[R], float &Us, float &Uc) {
+                                        int lane, int kahan, bool sum_u, float (&tot)[R], float &Us, float &Uc) {
     float ks[R], kc[R];
+    float2 u2[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) ks[r] = kc[r] = 0.0f;
-    Us = Uc = 0.0f;
+    for (int r = 0; r < R; ++r) {
+        ks[r] = kc[r] = 0.0f;
+        u2[r] = make_float2(ui[r], ui[r]);
+    }
+    float ns = 0.0f, nc = 0.0f;   // compensated sum of x = -u over this lane's columns
+    const float2 negm2 = make_float2(-m_shift, -m_shift);
+    const float2 negs2 = make_float2(-GJ_SCALE, -GJ_SCALE);
+    constexpr int BLK = 16;       // float4 loads per lane between Kahan folds
     for (int kt = 0; kt < sm.n_tiles; ++kt) {
         const int b = kt & 1;
         const int j0 = kt * TJ;
@@ -58,47 +108,24 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
             bar_uses[b]++;
             if (__syncthreads_or(!landed)) return false;   // block-uniform decision
         }
-        float *tb = sm.tile0 + b * sm.buf_len;
-        float4 *tb4w = reinterpret_cast<float4 *>(tb);
-        for (int j4 = threadIdx.x; j4 < (len >> 2); j4 += blockDim.x) {   // four columns per thread and round
-            const float4 v = tb4w[j4];
-            float x[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const bool real = j0 + 4 * j4 + q < n;
-                const float u = (x[q] - m_shift) * GJ_SCALE;
-                x[q] = real ? -u : -PAD_U;
-                if (real) kahan_add(Us, Uc, u);
-            }
-            tb4w[j4] = make_float4(x[0], x[1], x[2], x[3]);
-        }
-        __syncthreads();
+        const float *tb = sm.tile0 + b * sm.buf_len;
         const float4 *t4 = reinterpret_cast<const float4 *>(tb);
-        const int n4 = len >> 2;             // float4 columns; len is a multiple of 256
-        constexpr int BLK = 16;              // float4 loads per lane between Kahan folds
+        const int real = max(0, min(len, n - j0));   // real columns of this tile
+        const int n4 = (real + 3) >> 2;               // float4 columns that hold any
+        const int full4 = real >> 2;                  // float4 columns that hold only real ones
         for (int m0 = cs * 32 + lane; m0 < n4; m0 += 32 * GJ * BLK) {
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
-#pragma unroll 4
-            for (int mm = 0; mm < BLK; ++mm) {
-                const int m = m0 + mm * 32 * GJ;
-                if (m < n4) {
-                    const float4 v = t4[m];
-                    const float2 va = make_float2(v.x, v.y), vb = make_float2(v.z, v.w);
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float2 u2 = make_float2(ui[r], ui[r]);
-                        const float2 da = __fadd2_rn(u2, va);
-                        const float2 db = __fadd2_rn(u2, vb);
-                        const float2 qa = __fmul2_rn(da, da);
-                        const float2 qb = __fmul2_rn(db, db);
-                        const float2 ea = make_float2(ex2_approx(-qa.x), ex2_approx(-qa.y));
-                        const float2 eb = make_float2(ex2_approx(-qb.x), ex2_approx(-qb.y));
-                        acc[r] = __ffma2_rn(ea, da, acc[r]);
-                        acc[r] = __ffma2_rn(eb, db, acc[r]);
-                    }
-                }
+            float2 su = make_float2(0.0f, 0.0f);
+            // every column of the block is real: no per-column tests
+            const bool whole = m0 + (BLK - 1) * 32 * GJ < full4;
+            if (whole) {
+                if (sum_u) gj_block<R, GJ, BLK, true, false>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
+                else gj_block<R, GJ, BLK, false, false>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
+            } else {
+                if (sum_u) gj_block<R, GJ, BLK, true, true>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
+                else gj_block<R, GJ, BLK, false, true>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
             }
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -106,6 +133,7 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
                 if (kahan) kahan_add(ks[r], kc[r], blk);
                 else ks[r] += blk;
             }
+            if (sum_u) kahan_add(ns, nc, su.x + su.y);
         }
         // order this thread's generic accesses of the buffer before any later bulk refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -116,6 +144,8 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
     }
 #pragma unroll
     for (int r = 0; r < R; ++r) tot[r] = ks[r] - kc[r];
+    Us = -ns;   // sum of u = -(sum of x)
+    Uc = -nc;
     return true;
 }
 

@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "ion.h"
 #include "ion_async.cuh"
 #include "ion_model.cuh"
 
@@ -82,6 +83,114 @@ __device__ __forceinline__ void finish_cell(const StepCommon &a, int64_t t, floa
     if (a.trace != nullptr && ((t + 1) % a.trace_stride) == 0) {
         const int64_t sample = (t + 1) / a.trace_stride - 1;
         a.trace[(sample % a.trace_cap) * (int64_t)a.n + i] = o.va;
+    }
+}
+
+// ---- split cell update ------------------------------------------------------------------
+// The explicit-Euler update of one cell is a chain of ~36 SFU and ~300 FP32 operations when
+// one thread does it.  A CTA whose rows are few next to its threads (the dense step) spreads
+// each cell's outputs over NROLE threads instead: role 0 the dendrite (V_dend, [Ca], I_CaH,
+// I_c, s), 1 the soma voltage (and m_s), 2 the axon voltage (m_a, the trace sample), 3..9
+// the remaining gates.  Every role calls the same functions as cell_step, so a cell gets
+// the same bits either way.
+constexpr int NROLE = 10;
+constexpr int NCW = 15;   // words of Cell
+// state field of Cell word w (word 0, V_dend, comes from the step's V_dend slot)
+__device__ __forceinline__ int cell_word_field(int w) {
+    return w == 0 ? -1 : (w <= 8 ? w : (w <= 11 ? w + 1 : w + 2));
+}
+
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gsrc) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(smem_dst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Start copying the 15 Cell words of rows [row_base, row_base + rows) into cs[w * rows + r]
+// (all threads; waited for with cp_async_wait_all).  Rows at or past n are skipped.
+__device__ __forceinline__ void stage_cells(float *cs, const StateView &S, const float *vcur, int64_t row_base,
+                                            int rows, int n) {
+    for (int q = threadIdx.x; q < NCW * rows; q += blockDim.x) {
+        const int w = q / rows, r = q - w * rows;
+        const int64_t i = row_base + r;
+        if (i >= n) continue;
+        const float *src = w == 0 ? vcur : S.f(cell_word_field(w));
+        cp_async4(cs + q, src + i);
+    }
+    cp_async_commit();
+}
+
+__device__ __forceinline__ Cell staged_cell(const float *cs, int rows, int r) {
+    Cell c;
+    c.vd = cs[0 * rows + r];
+    c.vs = cs[1 * rows + r];
+    c.va = cs[2 * rows + r];
+    c.ca = cs[3 * rows + r];
+    c.r = cs[4 * rows + r];
+    c.s = cs[5 * rows + r];
+    c.q = cs[6 * rows + r];
+    c.k = cs[7 * rows + r];
+    c.l = cs[8 * rows + r];
+    c.hs = cs[9 * rows + r];
+    c.ns = cs[10 * rows + r];
+    c.xs = cs[11 * rows + r];
+    c.ha = cs[12 * rows + r];
+    c.xa = cs[13 * rows + r];
+    c.gcal = cs[14 * rows + r];
+    return c;
+}
+
+// Outputs of one role of cell i (see NROLE); iapp is read by role 0 only.
+__device__ __forceinline__ void cell_step_role(int role, const StepCommon &a, int64_t t, float *vd_next, int64_t i,
+                                               const Cell &c, float ic, float iapp) {
+    const ModelF &P = a.P;
+    const StateView &S = a.S;
+    const float dt = P.dt;
+    switch (role) {
+        case 0: {
+            const DendNext d = dend_step(P, c, ic, iapp);
+            vd_next[i] = d.vd;
+            S.f(F_CA)[i] = d.ca;
+            S.f(F_ICAH)[i] = d.icah;
+            S.f(F_IC)[i] = ic;
+            S.f(F_S)[i] = relax(c.s, rate_s(c.ca), dt);
+            if (!(isfinite(d.vd) && isfinite(d.ca))) atomicOr(a.status, (uint32_t)ST_NONFINITE);
+            if (a.par >= 0 && (int)(t & 1) != a.par) atomicOr(a.status, (uint32_t)ST_SLOT);
+            break;
+        }
+        case 1: {
+            const float ms = minf_na(c.vs);
+            const float vs = soma_step(P, c, ms);
+            S.f(F_VSOMA)[i] = vs;
+            S.f(F_MS)[i] = ms;
+            if (!isfinite(vs)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
+            break;
+        }
+        case 2: {
+            const float ma = minf_na(c.va);
+            const float va = axon_step(P, c, ma);
+            S.f(F_VAXON)[i] = va;
+            S.f(F_MA)[i] = ma;
+            if (!isfinite(va)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
+            if (a.trace != nullptr && ((t + 1) % a.trace_stride) == 0) {
+                const int64_t sample = (t + 1) / a.trace_stride - 1;
+                a.trace[(sample % a.trace_cap) * (int64_t)a.n + i] = va;
+            }
+            break;
+        }
+        case 3: S.f(F_R)[i] = relax(c.r, rate_r(c.vd), dt); break;
+        case 4: S.f(F_Q)[i] = relax(c.q, rate_q(c.vd), dt); break;
+        case 5:
+            S.f(F_K)[i] = relax(c.k, rate_k(c.vs), dt);
+            S.f(F_HS)[i] = relax(c.hs, rate_hs(c.vs), dt);
+            break;
+        case 6: S.f(F_L)[i] = relax(c.l, rate_l(c.vs), dt); break;
+        case 7:
+            S.f(F_NS)[i] = relax(c.ns, rate_ns(c.vs), dt);
+            S.f(F_HA)[i] = relax(c.ha, rate_ha(c.va), dt);
+            break;
+        case 8: S.f(F_XS)[i] = relax(c.xs, rate_x(c.vs), dt); break;
+        default: S.f(F_XA)[i] = relax(c.xa, rate_x(c.va), dt); break;
     }
 }
 
@@ -175,5 +284,13 @@ int persist_max_threads(int rows_per_warp);   // thread limit of the persistent 
 
 // shared-memory size of a dense launch
 size_t dense_smem_bytes(int n_pad, int rows_per_warp, int warps);
+
+// surrogate inference on tcgen05 (ion_mlp_tc.cu): packed weights, cell kernel, batched eval
+size_t surrogate_tc_weights_bytes();
+cudaError_t surrogate_tc_prepare();
+cudaError_t surrogate_tc_pack(const ion_surrogate_weights *d_w, void *d_out, cudaStream_t st);
+cudaError_t launch_surrogate_tc(const StepCommon &c, const void *W, const float *ic, cudaStream_t st);
+cudaError_t launch_mlp_eval_tc(const void *W, int64_t n, const float *V, const float *ca, float *out,
+                               uint32_t *status, cudaStream_t st);
 
 }  // namespace ion

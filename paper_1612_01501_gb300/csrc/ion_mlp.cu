@@ -15,8 +15,10 @@
 // one launch of mlp_adam_kernel (sums the partials in a fixed order, then the Adam step
 // on FP32 master weights), so training is deterministic.
 //
-// Inference (ion_surrogate_eval and the surrogate cell update) runs on the tensor cores:
-// BF16 weights and activations, FP32 accumulation, mma.sync m16n8k16.  Layer 1 (two
+// Inference runs on the tensor cores, BF16 weights and activations with FP32 accumulation:
+// by default on tcgen05 with TMEM accumulators (ion_mlp_tc.cu: ion_surrogate_eval and the
+// cell update); with ION_FLAG_SURROGATE_WARP_MMA the cell update below uses mma.sync
+// m16n8k16 instead (kept for comparison).  Layer 1 (two
 // inputs) is FP32 FMAs; the 64x64 and 64x24 layers are MMAs whose accumulator fragments
 // become the next layer's A fragments in registers; tanh runs on packed bf16 pairs.
 // The cell kernel evaluates one row per (cell, compartment) -- 96 rows per warp for 32
@@ -426,35 +428,6 @@ __device__ __forceinline__ void load_mlp(MlpDev &dst, const MlpDev *src) {
     for (int i = threadIdx.x; i < (int)(sizeof(MlpDev) / 16); i += blockDim.x) d[i] = s[i];
 }
 
-// Evaluate the surrogate for n (V, ca) pairs: out[k * 24 + o], physical units.
-__global__ void __launch_bounds__(128) mlp_eval_kernel(const MlpDev *Wg, int64_t n, const float *V, const float *ca,
-                                                       float *out) {
-    __shared__ __align__(16) MlpDev W;
-    load_mlp(W, Wg);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
-    const int64_t r0 = ((int64_t)blockIdx.x * 4 + warp) * 16;
-    const int64_t ra = r0 + g, rb = r0 + g + 8;
-    const float a0 = ra < n ? (V[ra] - W.in_shift[0]) * W.in_scale[0] : 0.0f;
-    const float a1 = ra < n ? (logf(ca[ra]) - W.in_shift[1]) * W.in_scale[1] : 0.0f;
-    const float c0 = rb < n ? (V[rb] - W.in_shift[0]) * W.in_scale[0] : 0.0f;
-    const float c1 = rb < n ? (logf(ca[rb]) - W.in_shift[1]) * W.in_scale[1] : 0.0f;
-    float y[3][4];
-    mlp_mtile(W, a0, a1, c0, c1, y);
-#pragma unroll
-    for (int nt = 0; nt < 3; ++nt) {
-        const int o = 8 * nt + 2 * t;
-        if (ra < n) {
-            out[ra * MO + o] = y[nt][0];
-            out[ra * MO + o + 1] = y[nt][1];
-        }
-        if (rb < n) {
-            out[rb * MO + o] = y[nt][2];
-            out[rb * MO + o + 1] = y[nt][3];
-        }
-    }
-}
-
 // ---- the cell update with learned rates ------------------------------------------------------
 // 64 threads; warp w owns CPW = 16 cells [base, base + 16): rows 0..15 dendrite (V_dend,
 // [Ca]), 16..31 soma (V_soma, [Ca]), 32..47 axon (V_axon, [Ca]); three m-tiles of 16 rows.
@@ -703,52 +676,63 @@ extern "C" ion_status ion_surrogate_grad(const ion_surrogate_weights *w, const f
     return ION_OK;
 }
 
-// Upload a surrogate (host struct) as the packed inference copy.
-ion_status ion_mlp_upload(const ion_surrogate_weights *w, void **d_out, cudaStream_t st) {
+// Upload a surrogate (host struct) as the packed inference copies: the warp-MMA layout
+// (*d_out, may be NULL) and the tcgen05 layout (*d_tc).
+ion_status ion_mlp_upload(const ion_surrogate_weights *w, void **d_out, void **d_tc, cudaStream_t st) {
     ion_surrogate_weights *dw = nullptr;
     MlpDev *d = nullptr;
+    void *t = nullptr;
     cudaError_t e = ion_alloc(&dw, sizeof *dw);
-    if (e == cudaSuccess) e = ion_alloc(&d, sizeof *d);
+    if (e == cudaSuccess && d_out) e = ion_alloc(&d, sizeof *d);
+    if (e == cudaSuccess) e = ion_alloc(&t, surrogate_tc_weights_bytes());
     if (e == cudaSuccess) e = cudaMemcpyAsync(dw, w, sizeof *dw, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && d_out) {
         mlp_pack_kernel<<<1, 256, 0, st>>>(dw, d);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) e = surrogate_tc_pack(dw, t, st);
+    if (e == cudaSuccess) e = surrogate_tc_prepare();
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(dw);
     if (e != cudaSuccess) {
         cudaFree(d);
+        cudaFree(t);
         return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "surrogate upload: %s",
                         cudaGetErrorString(e));
     }
-    *d_out = d;
+    if (d_out) *d_out = d;
+    *d_tc = t;
     return ION_OK;
 }
 
 extern "C" ion_status ion_surrogate_eval(const ion_surrogate_weights *w, const float *V, const float *ca, int64_t n,
                                          float *out) {
     if (!w || !V || !ca || !out || n < 1) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "ion_surrogate_eval: bad arguments");
-    void *d = nullptr;
-    ion_status st = ion_mlp_upload(w, &d, nullptr);
+    void *t = nullptr;
+    ion_status st = ion_mlp_upload(w, nullptr, &t, nullptr);
     if (st != ION_OK) return st;
     float *dV = nullptr, *dc = nullptr, *dout = nullptr;
+    uint32_t *dstat = nullptr;
     cudaError_t e = ion_alloc(&dV, n * 4);
     if (e == cudaSuccess) e = ion_alloc(&dc, n * 4);
     if (e == cudaSuccess) e = ion_alloc(&dout, n * MO * 4);
+    if (e == cudaSuccess) e = ion_alloc(&dstat, 4);
+    if (e == cudaSuccess) e = cudaMemset(dstat, 0, 4);
     if (e == cudaSuccess) e = cudaMemcpy(dV, V, n * 4, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(dc, ca, n * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) {
-        mlp_eval_kernel<<<(unsigned)((n + 63) / 64), 128>>>((const MlpDev *)d, n, dV, dc, dout);
-        e = cudaGetLastError();
-    }
+    if (e == cudaSuccess) e = launch_mlp_eval_tc(t, n, dV, dc, dout, dstat, nullptr);
+    uint32_t hstat = 0;
     if (e == cudaSuccess) e = cudaMemcpy(out, dout, n * MO * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&hstat, dstat, 4, cudaMemcpyDeviceToHost);
     cudaFree(dV);
     cudaFree(dc);
     cudaFree(dout);
-    cudaFree(d);
+    cudaFree(dstat);
+    cudaFree(t);
     if (e != cudaSuccess)
         return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "ion_surrogate_eval: %s",
                         cudaGetErrorString(e));
+    if (hstat & ST_TIMEOUT) return ion_fail(nullptr, ION_ERR_TIMEOUT, "ion_surrogate_eval: a tensor-core wait timed out");
     return ION_OK;
 }
 
@@ -777,15 +761,17 @@ static cudaError_t surrogate_step(ion_sim *s, int k_off, const float *iapp) {
         s->launches++;
     }
     if (e != cudaSuccess) return e;
-    SurrArgs sa{c, (const MlpDev *)s->d_mlp, s->kind == ION_NO_GJ ? nullptr : s->d_ic};
     s->launches++;
+    const float *ic = s->kind == ION_NO_GJ ? nullptr : s->d_ic;
+    if (!(s->flags & ION_FLAG_SURROGATE_WARP_MMA)) return launch_surrogate_tc(c, s->d_mlp_tc, ic, s->st);
+    SurrArgs sa{c, (const MlpDev *)s->d_mlp, ic};
     return launch_k(surrogate_cell_kernel, dim3((unsigned)((s->n + 2 * SURR_CPW - 1) / (2 * SURR_CPW))), dim3(64), 0,
                     s->st, c.pdl != 0, sa);
 }
 
 ion_status ion_setup_surrogate(ion_sim *s, const ion_params *p) {
     if (!p->surrogate) return ion_fail(nullptr, ION_ERR_INVALID_ARG, "surrogate: no weights");
-    ion_status st = ion_mlp_upload((const ion_surrogate_weights *)p->surrogate, &s->d_mlp, s->st);
+    ion_status st = ion_mlp_upload((const ion_surrogate_weights *)p->surrogate, &s->d_mlp, &s->d_mlp_tc, s->st);
     if (st != ION_OK) return st;
     if (s->kind != ION_NO_GJ && !s->d_ic) {
         cudaError_t e = ion_alloc(&s->d_ic, (size_t)s->n_pad * sizeof(float));

@@ -185,26 +185,25 @@ __device__ __forceinline__ CellRates exact_rates(const Cell &c) {
     return g;
 }
 
-// One explicit-Euler step of one cell given its gates' rates (exact or learned).
-__device__ __forceinline__ CellNext cell_step_rates(const ModelF &P, const Cell &c, float ic, float iapp,
-                                                    const CellRates &g) {
-    CellNext o;
-    const float dt = P.dt;
-    // dendrite
+// ---- the three compartment voltages (and [Ca]) of one explicit-Euler step ---------
+// Each function computes its outputs from the step-t cell alone.  The single-thread step
+// below and the split update (one cell's outputs spread over several threads, see
+// ion_kernels.cuh) both call them, so either way a cell gets the same bits.
+struct DendNext { float vd, ca, icah; };
+__device__ __forceinline__ DendNext dend_step(const ModelF &P, const Cell &c, float ic, float iapp) {
+    DendNext o;
     const float I_CaH = P.gCaH * c.r * c.r * (c.vd - P.VCa);
     const float I_KCa = P.gKCa * c.s * (c.vd - P.VK);
     const float I_h = P.gh * c.q * (c.vd - P.Vh);
     const float I_ld = P.gld * (c.vd - P.VL);
     const float I_ds = P.g_ds * (c.vd - c.vs);
     o.vd = fmaf(P.dt_cm, iapp - I_CaH - I_KCa - I_h - I_ld - I_ds - ic, c.vd);
-    o.ca = fmaf(dt, -P.ca_in * I_CaH - P.ca_out * c.ca, c.ca);
-    o.r = relax(c.r, g.r, dt);
-    o.s = relax(c.s, g.s, dt);
-    o.q = relax(c.q, g.q, dt);
+    o.ca = fmaf(P.dt, -P.ca_in * I_CaH - P.ca_out * c.ca, c.ca);
     o.icah = I_CaH;
-    o.ic = ic;
-    // soma
-    const float ms = g.ms.xinf;
+    return o;
+}
+// ms = m_inf(V_soma) of step t
+__device__ __forceinline__ float soma_step(const ModelF &P, const Cell &c, float ms) {
     const float k3 = c.k * c.k * c.k;
     const float n2 = c.ns * c.ns, x2 = c.xs * c.xs;
     const float I_CaL = c.gcal * k3 * c.l * (c.vs - P.VCa);
@@ -214,22 +213,40 @@ __device__ __forceinline__ CellNext cell_step_rates(const ModelF &P, const Cell 
     const float I_ls = P.gls * (c.vs - P.VL);
     const float I_sd = P.g_sd * (c.vs - c.vd);
     const float I_sa = P.g_sa * (c.vs - c.va);
-    o.vs = fmaf(-P.dt_cm, I_CaL + I_Nas + I_Kdr + I_Ks + I_ls + I_sd + I_sa, c.vs);
-    o.k = relax(c.k, g.k, dt);
-    o.l = relax(c.l, g.l, dt);
-    o.ms = ms;
-    o.hs = relax(c.hs, g.hs, dt);
-    o.ns = relax(c.ns, g.ns, dt);
-    o.xs = relax(c.xs, g.xs, dt);
-    // axon
-    const float ma = g.ma.xinf;
+    return fmaf(-P.dt_cm, I_CaL + I_Nas + I_Kdr + I_Ks + I_ls + I_sd + I_sa, c.vs);
+}
+// ma = m_inf(V_axon) of step t
+__device__ __forceinline__ float axon_step(const ModelF &P, const Cell &c, float ma) {
     const float xa2 = c.xa * c.xa;
     const float I_Naa = P.gNaa * ma * ma * ma * c.ha * (c.va - P.VNa);
     const float I_Ka = P.gKa * xa2 * xa2 * (c.va - P.VK);
     const float I_la = P.gla * (c.va - P.VL);
     const float I_as = P.g_as * (c.va - c.vs);
-    o.va = fmaf(-P.dt_cm, I_Naa + I_Ka + I_la + I_as, c.va);
-    o.ma = ma;
+    return fmaf(-P.dt_cm, I_Naa + I_Ka + I_la + I_as, c.va);
+}
+
+// One explicit-Euler step of one cell given its gates' rates (exact or learned).
+__device__ __forceinline__ CellNext cell_step_rates(const ModelF &P, const Cell &c, float ic, float iapp,
+                                                    const CellRates &g) {
+    CellNext o;
+    const float dt = P.dt;
+    const DendNext d = dend_step(P, c, ic, iapp);
+    o.vd = d.vd;
+    o.ca = d.ca;
+    o.icah = d.icah;
+    o.ic = ic;
+    o.r = relax(c.r, g.r, dt);
+    o.s = relax(c.s, g.s, dt);
+    o.q = relax(c.q, g.q, dt);
+    o.ms = g.ms.xinf;
+    o.vs = soma_step(P, c, o.ms);
+    o.k = relax(c.k, g.k, dt);
+    o.l = relax(c.l, g.l, dt);
+    o.hs = relax(c.hs, g.hs, dt);
+    o.ns = relax(c.ns, g.ns, dt);
+    o.xs = relax(c.xs, g.xs, dt);
+    o.ma = g.ma.xinf;
+    o.va = axon_step(P, c, o.ma);
     o.ha = relax(c.ha, g.ha, dt);
     o.xa = relax(c.xa, g.xa, dt);
     return o;
@@ -248,6 +265,28 @@ struct StateView {
     int64_t stride;     // >= n, multiple of 4
     __device__ __forceinline__ float *f(int field) const { return base + field * stride; }
 };
+
+// The 15 words of cell i, V_dend given (persistent launches read it from a staged copy)
+__device__ __forceinline__ Cell load_cell(const StateView &S, const float *vd_cur, int64_t i, float vd) {
+    (void)vd_cur;
+    Cell c;
+    c.vd = vd;
+    c.vs = S.f(F_VSOMA)[i];
+    c.va = S.f(F_VAXON)[i];
+    c.ca = S.f(F_CA)[i];
+    c.r = S.f(F_R)[i];
+    c.s = S.f(F_S)[i];
+    c.q = S.f(F_Q)[i];
+    c.k = S.f(F_K)[i];
+    c.l = S.f(F_L)[i];
+    c.hs = S.f(F_HS)[i];
+    c.ns = S.f(F_NS)[i];
+    c.xs = S.f(F_XS)[i];
+    c.ha = S.f(F_HA)[i];
+    c.xa = S.f(F_XA)[i];
+    c.gcal = S.f(F_GCAL)[i];
+    return c;
+}
 
 __device__ __forceinline__ Cell load_cell(const StateView &S, const float *vd_cur, int64_t i) {
     Cell c;

@@ -71,7 +71,8 @@ struct ion_sim {
     int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk
     int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
     int32_t *d_mid = nullptr;       // interior chunk boundaries per row
-    void *d_mlp = nullptr;          // packed surrogate weights (ION_FLAG_SURROGATE)
+    void *d_mlp = nullptr;          // packed surrogate weights (ION_FLAG_SURROGATE), warp-MMA layout
+    void *d_mlp_tc = nullptr;       // the same weights in the tcgen05 kernels' layout
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // K-step graphs, by the parity of their first step
     int64_t t_enq = 0;              // the device step counter's value where the next launch is enqueued
     int64_t graph_launches = 0;
@@ -86,6 +87,7 @@ struct ion_sim {
     ion_status (*state_sync_hook)(ion_sim *) = nullptr;
     ion_status (*state_load_hook)(ion_sim *) = nullptr;
     void (*extra_free)(ion_sim *) = [](ion_sim *) {};
+    void (*drop_hook)(ion_sim *) = nullptr;   // drops graphs an extension captured
     void *ext = nullptr;            // extension state
     int64_t lps = 1;                // kernel launches per step
 
@@ -122,6 +124,7 @@ inline void ion_drop_graphs(ion_sim *s) {
         if (g) cudaGraphExecDestroy(g);
         g = nullptr;
     }
+    if (s->drop_hook) s->drop_hook(s);
 }
 // per-flag setup of the extensions (ion_ext.cu)
 ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p);

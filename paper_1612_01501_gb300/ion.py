@@ -30,6 +30,7 @@ FLAG_KAHAN, FLAG_PERSISTENT, FLAG_SURROGATE, FLAG_CHECKS, FLAG_NO_GRAPH, FLAG_SP
 FLAG_CSR_AS_GIVEN = 128
 FLAG_SGJ = 256           # SGJ use case: linear junctions w (V_i - V_j)
 FLAG_NO_PDL = 512        # ordinary launches instead of programmatic dependent launches
+FLAG_SURROGATE_WARP_MMA = 1024   # surrogate MLP on warp-level mma.sync instead of tcgen05
 INPUT_NONE, INPUT_PULSES, INPUT_DENSE = 0, 1, 2
 MLP_IN, MLP_HID, MLP_OUT = 2, 64, 24
 

@@ -245,3 +245,103 @@ def test_autotune_single_network(cuda, O, kind):
              col=kw.get("col"), w=kw.get("w"))
     ref = _oracle_net(O, b, S0, 100, None)
     assert np.abs(got[:3] - ref[:3]).max() <= TRAJ_MV
+
+
+# ------------------------------------------------------------------ persistent batches
+
+def test_persistent_batch_bitwise_equals_step_launches(cuda, O):
+    """One cooperative launch per ion_step call (pieces dealt to resident CTAs, per-network
+    arrival counters) gives the per-step launches' states bit for bit, with pulses, over
+    several calls of different lengths."""
+    nets = _nets(_mixed_specs())
+    S0, pul = _batch_inputs(O, nets)
+    out = []
+    for flags in (ion.FLAG_KAHAN, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT):
+        h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=flags, graph_steps=50)
+        try:
+            ion.ion_set_input(h, pul)
+            for k in (1, 299, 300, 7):
+                ion.ion_step(h, k)
+            out.append(ion.ion_read_state(h, S0.shape[1]))
+            launches = ion.ion_launch_count(h)
+        finally:
+            ion.ion_destroy(h)
+    np.testing.assert_array_equal(out[0], out[1])
+    assert launches == 8      # a kernel and a counter advance per call
+
+
+@pytest.mark.parametrize("R", [1, 2, 4])
+def test_persistent_batch_shapes_one_step(cuda, O, R):
+    """One step of the mixed batch through the persistent kernel at each dense row count,
+    against the oracle (per-step bar)."""
+    nets = _nets(_mixed_specs())
+    S0, _ = _batch_inputs(O, nets)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
+                             tune=dict(dense_rows_per_warp=R))
+    try:
+        ion.ion_step(h, 1)
+        got = ion.ion_read_state(h, S0.shape[1])
+    finally:
+        ion.ion_destroy(h)
+    off = 0
+    for b in nets:
+        n = b["n"]
+        ref = _oracle_net(O, b, S0[:, off:off + n], 1, None)
+        scale = b["g"] * sum_abs_dv(S0[0, off:off + n]) if b["kind"] == "dense" else \
+            csr_abs_scale(b["row_ptr"], b["col"], b["w"], S0[0, off:off + n])
+        err = step_rel_err(got[:, off:off + n], ref, scale)
+        assert err.max() <= STEP_RTOL, (R, b["spec"], err.max(axis=1))
+        off += n
+
+
+def test_persistent_c4_all_256_networks(cuda, O):
+    """The 256-network batch in the persistent form: 100 steps equal the per-step launches
+    bit for bit, and one step of every network meets the per-step bar against the oracle."""
+    nets = _nets(inputs.batch_specs())
+    S0, pul = _batch_inputs(O, nets)
+    res = []
+    for flags in (ion.FLAG_KAHAN, ion.FLAG_KAHAN | ion.FLAG_PERSISTENT):
+        h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=flags, graph_steps=50)
+        try:
+            ion.ion_step(h, 1)
+            one = ion.ion_read_state(h, S0.shape[1])
+            ion.ion_set_input(h, pul)
+            ion.ion_step(h, 100)
+            res.append((one, ion.ion_read_state(h, S0.shape[1])))
+        finally:
+            ion.ion_destroy(h)
+    np.testing.assert_array_equal(res[0][1], res[1][1])
+    got = res[1][0]
+    offs = np.concatenate([[0], np.cumsum([b["n"] for b in nets])])
+    for i, b in enumerate(nets):
+        sl = slice(offs[i], offs[i + 1])
+        ref = _oracle_net(O, b, S0[:, sl], 1, None)
+        scale = b["g"] * sum_abs_dv(S0[0, sl]) if b["kind"] == "dense" else \
+            csr_abs_scale(b["row_ptr"], b["col"], b["w"], S0[0, sl])
+        err = step_rel_err(got[:, sl], ref, scale)
+        assert err.max() <= STEP_RTOL, (i, b["spec"], err.max(axis=1))
+
+
+def test_persistent_batch_wait_timeout_is_reported(cuda, O):
+    """CTA 0 sleeps 200 ms before its first piece while a wait is bounded by 1 ms: the
+    CTAs waiting for its network's arrivals give up, raise the abort word and return; the
+    host sees ION_ERR_TIMEOUT and the context stays usable."""
+    specs = [dict(n=4096, kind="dense", k=4096, g_ref=0.02, seed=31), dict(n=2000, kind="dense", k=2000,
+                                                                           g_ref=0.02, seed=32)]
+    nets = _nets(specs)
+    S0, _ = _batch_inputs(O, nets)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT,
+                             barrier_timeout_ns=1_000_000, debug_delay_ns=200_000_000)
+    try:
+        ion.ion_step(h, 5)
+        with pytest.raises(ion.IonError) as ei:
+            ion.ion_sync(h)
+        assert ei.value.status == ion.ERR_TIMEOUT
+    finally:
+        ion.ion_destroy(h)
+    h = ion.ion_create_batch(_ion_nets(nets), init_state=S0, flags=ion.FLAG_KAHAN | ion.FLAG_PERSISTENT)
+    try:
+        ion.ion_step(h, 5)
+        ion.ion_sync(h)
+    finally:
+        ion.ion_destroy(h)
