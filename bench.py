@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--sim-steps", type=int, default=0, help="time steps per bench step (0: the workload's)")
     ap.add_argument("--variant", default="auto",
-                    choices=["auto", "graph", "persistent", "persistent_half", "graph_csr_as_given"])
+                    choices=["auto", "graph", "persistent", "persistent_half", "graph_csr_as_given", "graph_csr_half"])
     ap.add_argument("--no-extra", action="store_true", help="skip the CPU baseline and the e2e leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the library's default launch shapes")
     ap.add_argument("--dense-shape", default="", help="R,W,GJ: a fixed dense launch shape (no autotuning)")
@@ -460,6 +460,7 @@ def main():
             cand.append(("persistent_half", ion.FLAG_KAHAN | ion.FLAG_PERSISTENT | ion.FLAG_HALF_WORK))
     if cfg["kind"] == "csr" and key != "c5":   # the CSR as given (32-bit columns, per-edge weights) too
         cand.append(("graph_csr_as_given", ion.FLAG_KAHAN | ion.FLAG_CSR_AS_GIVEN))
+        cand.append(("graph_csr_half", ion.FLAG_KAHAN | ion.FLAG_HALF_WORK))   # each stored pair once
     if args.variant != "auto":
         cand = [c for c in cand if c[0] == args.variant]
     if key == "c5":

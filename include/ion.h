@@ -99,9 +99,13 @@ enum ion_flag {
     ION_FLAG_CHECKS = 1u << 3,     /* non-finite scan of every cell every check_every steps */
     ION_FLAG_NO_GRAPH = 1u << 4,   /* launch steps directly instead of CUDA-graph replay    */
     ION_FLAG_SPLIT = 1u << 5,      /* separate gap-junction and cell-update kernels         */
-    ION_FLAG_HALF_WORK = 1u << 6,  /* persistent dense with several CTAs: evaluate each unordered
-                                      pair once (I_ij = -I_ji), exchanging column sums through
-                                      L2 (two bounded barriers per step)                     */
+    ION_FLAG_HALF_WORK = 1u << 6,  /* evaluate each unordered pair once (I_ij = -I_ji).  Dense,
+                                      with PERSISTENT and several CTAs: column sums exchanged
+                                      through L2 (two bounded barriers per step).  CSR (host
+                                      arrays, symmetric weights): the upper triangle only,
+                                      each mirrored term through a per-edge slot, then a
+                                      fixed-order gather per row (two launches per step; not
+                                      with SPLIT, SGJ, PERSISTENT or SURROGATE)            */
     ION_FLAG_CSR_AS_GIVEN = 1u << 7, /* CSR: keep 32-bit columns and per-edge weights even when
                                       a compact layout applies (see ion_csr_layout)         */
     ION_FLAG_SGJ = 1u << 8,        /* SGJ use case (Sec. 2.3.2): each connection contributes

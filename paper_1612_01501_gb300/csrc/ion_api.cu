@@ -305,7 +305,7 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
 // cells) and the direct kernel when n <= 65 536 and rows are long enough (mean degree >= 32)
 // for its eight-edge groups; shorter rows read 32-bit columns four at a time.
 static bool csr_use16(const ion_sim *s, bool staged) {
-    if (s->d_col16 == nullptr) return false;
+    if (s->d_col16 == nullptr || s->d_rev != nullptr) return false;   // the half-work passes read 32-bit columns
     return staged || (s->n <= 65536 && s->nnz >= 32 * (int64_t)s->n);
 }
 
@@ -324,7 +324,7 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     const bool on = mode == 2 || (mode == 0 && deg >= 64.0 && csr_bytes > 96.0e6);
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
-    if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr) return ION_OK;
+    if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr || s->d_rev) return ION_OK;
     s->n_chunks = (s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK;
     int rows = (s->n + s->sms - 1) / s->sms;
     if (rows > 1024) rows = 1024;
@@ -360,6 +360,44 @@ ion_status ion_prepare_csr_chunk(ion_sim *s) {
 // ---- creation -------------------------------------------------------------------------
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Half-work CSR: per row the first upper edge, per upper edge the position of its mirror
+// (host binary search in the sorted rows), the slot and upper-sum buffers.  Needs a host
+// CSR with symmetric weights (checked bit for bit).
+ion_status ion_setup_csr_half(ion_sim *s, const ion_conn *conn) {
+    if (conn->mem != ION_HOST)
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "half-work CSR needs host arrays");
+    if (s->flags & (ION_FLAG_SPLIT | ION_FLAG_SGJ | ION_FLAG_PERSISTENT | ION_FLAG_SURROGATE))
+        return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "half-work CSR: not with SPLIT, SGJ, PERSISTENT or SURROGATE");
+    const int32_t n = s->n, *rp = conn->row_ptr, *col = conn->col_idx;
+    std::vector<int32_t> split((size_t)n), rev((size_t)std::max<int64_t>(s->nnz, 1), 0);
+    for (int32_t i = 0; i < n; ++i) {
+        split[(size_t)i] = (int32_t)(std::upper_bound(col + rp[i], col + rp[i + 1], i) - col);
+        for (int32_t e = split[(size_t)i]; e < rp[i + 1]; ++e) {
+            const int32_t j = col[e];
+            const int32_t m = (int32_t)(std::lower_bound(col + rp[j], col + rp[j + 1], i) - col);   // (j, i)
+            if (conn->weight) {
+                uint32_t a, b;
+                std::memcpy(&a, conn->weight + e, 4);
+                std::memcpy(&b, conn->weight + m, 4);
+                if (a != b) return ion_fail(nullptr, ION_ERR_UNSUPPORTED, "half-work CSR needs symmetric weights");
+            }
+            rev[(size_t)e] = m;
+        }
+    }
+    cudaError_t e = ion_alloc(&s->d_split, (size_t)n * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_rev, rev.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_slot, rev.size() * sizeof(float));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_icu, (size_t)s->n_pad * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_split, split.data(), split.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_rev, rev.data(), rev.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);   // the host vectors go out of scope
+    if (e != cudaSuccess)
+        return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "half-work CSR setup: %s",
+                        cudaGetErrorString(e));
+    s->lps = 2;
+    return ION_OK;
+}
+
 void ion_sim_free_device(ion_sim *s) {
     ion_drop_graphs(s);
     cudaFree(s->d_state);
@@ -386,6 +424,12 @@ void ion_sim_free_device(ion_sim *s) {
     cudaFree(s->d_ic);
     cudaFree(s->d_cellp);
     s->d_cellp = nullptr;
+    cudaFree(s->d_split);
+    cudaFree(s->d_rev);
+    cudaFree(s->d_slot);
+    cudaFree(s->d_icu);
+    s->d_split = s->d_rev = nullptr;
+    s->d_slot = s->d_icu = nullptr;
     cudaFree(s->d_mid);
     cudaFree(s->d_mlp);
     cudaFree(s->d_mlp_tc);
@@ -579,6 +623,10 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
                     e = launch_csr_col16(s->d_col, s->nnz, round_up(s->nnz, 8), s->d_col16, s->st);
             }
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: CSR copy: %s", cudaGetErrorString(e)));
+        }
+        if (s->flags & ION_FLAG_HALF_WORK) {
+            const ion_status hs = ion_setup_csr_half(s, conn);
+            if (hs != ION_OK) return fail(hs);
         }
         int SW, rows;
         ion_choose_csr_shape((double)s->nnz / s->n, &SW, &rows);
@@ -788,6 +836,16 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
             e = launch_cell_step(ca, s->st);
             s->launches++;
         }
+    } else if (s->kind == ION_CSR && s->d_rev) {   // half-work: upper pass, then lower pass + update
+        CsrArgs a{};
+        a.c = c;
+        a.row_ptr = s->d_rowptr;
+        a.col = s->d_col;
+        a.w = s->d_w;
+        a.g = s->g;
+        a.fuse = 1;
+        e = launch_csr_half_step(a, s->csr_SW, s->csr_rows, s->d_split, s->d_rev, s->d_slot, s->d_icu, s->st);
+        s->launches += 2;
     } else if (s->kind == ION_CSR) {
         CsrArgs a{};
         a.c = c;

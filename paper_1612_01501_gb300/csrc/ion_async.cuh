@@ -131,4 +131,52 @@ __device__ __forceinline__ bool grid_barrier(uint32_t *count, uint32_t *abort_fl
     return *ok_sh != 0;
 }
 
+// ---- grid-wide barrier with a release flag (bounded) ------------------------------------
+__device__ __forceinline__ uint32_t atom_add_acqrel_gpu(uint32_t *p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ void st_release_gpu(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Every CTA arrives once on `count` (acquire-release); the CTA that brings it to `target`
+// (mod 2^32) is the last and stores `target` to `flag` (release); the others poll `flag`,
+// which lives on its own cache line, until it reaches `target`.  So the arrivals are not
+// slowed by pollers on their line, and a poll sees the release of one store.  Bounded
+// like grid_barrier (timeout_ns or 2^30 polls: status bit 2 and the abort word).
+__device__ __forceinline__ bool grid_barrier_flag(uint32_t *count, uint32_t *flag, uint32_t *abort_flag,
+                                                  uint32_t target, uint64_t timeout_ns, uint32_t *status, int *ok_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint32_t old = atom_add_acqrel_gpu(count, 1u);
+        if (old + 1u == target) {
+            st_release_gpu(flag, target);
+        } else if (!arrivals_reached(ld_acquire_gpu(flag), target)) {
+            const uint64_t t0 = globaltimer_ns();
+            for (uint32_t it = 1;; ++it) {
+                if (arrivals_reached(ld_acquire_gpu(flag), target)) break;
+                if ((it & 63u) == 0u) {
+                    if (ld_acquire_gpu(abort_flag) != 0u) {
+                        ok = 0;
+                        break;
+                    }
+                    if (globaltimer_ns() - t0 > timeout_ns || it > (1u << 30)) {
+                        atomicOr(status, 2u);
+                        atomicExch(abort_flag, 1u);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        asm volatile("fence.proxy.async;" ::: "memory");
+        *ok_sh = ok;
+    }
+    __syncthreads();
+    return *ok_sh != 0;
+}
+
 }  // namespace ion

@@ -442,6 +442,102 @@ cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st) {
     return launch_k(sgj_csr_step_kernel, dim3((a.c.n + 31) / 32), dim3(256), 0, st, a.c.pdl != 0, a);
 }
 
+// ---- half-work CSR (each stored pair evaluated once) ------------------------------------
+// The pair term is odd in dV and the weights are symmetric, so the term of the stored edge
+// (j, i) is exactly the negated term of (i, j).  Pass 1 walks the upper triangle: for each
+// edge e = (i, j), j > i, it adds t_e to row i and writes -t_e into slot[rev[e]], the
+// position of the mirrored edge (j, i) in row j (every slot is written by exactly one
+// edge: no atomics).  Pass 2 adds to each row the slots of its lower edges, in a fixed
+// order, and runs the cell update.  split[i] is the first edge of row i with col > i.
+template <int SW, bool HAS_W>
+__global__ void __launch_bounds__(256) csr_half_upper_kernel(const CsrArgs a, int rows, const int32_t *split,
+                                                             const int32_t *rev, float *slot, float *icu) {
+    pdl_enter();
+    const StepCommon &c = a.c;
+    const float *vcur = vd_cur(c);
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    const int row0 = blockIdx.x * rows;
+    for (int rr = sub; rr - sub < rows; rr += nsub) {   // the same trip count in every lane
+        const int i = row0 + rr;
+        float acc = 0.0f;
+        if (rr < rows && i < c.n) {
+            const float vi = vcur[i];
+            for (int e = split[i] + li; e < a.row_ptr[i + 1]; e += SW) {
+                const float t = gj_edge(vi, __ldg(vcur + __ldg(a.col + e)), HAS_W ? __ldg(a.w + e) : 1.0f);
+                acc += t;
+                slot[__ldg(rev + e)] = -t;
+            }
+        }
+#pragma unroll
+        for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (li == 0 && rr < rows && i < c.n) icu[i] = acc;
+    }
+}
+
+template <int SW, bool HAS_W>
+__global__ void __launch_bounds__(256) csr_half_lower_kernel(const CsrArgs a, int rows, const int32_t *split,
+                                                             const float *slot, const float *icu) {
+    __shared__ float ic_s[256];
+    pdl_enter();
+    const StepCommon &c = a.c;
+    const int64_t t = step_index(c);
+    const float *vcur = vd_cur(c);
+    float *vnext = vd_next(c);
+    const int sub = threadIdx.x / SW, li = threadIdx.x % SW, nsub = blockDim.x / SW;
+    const int row0 = blockIdx.x * rows;
+    for (int rr = sub; rr - sub < rows; rr += nsub) {
+        const int i = row0 + rr;
+        float acc = 0.0f;
+        if (rr < rows && i < c.n)
+            for (int e = a.row_ptr[i] + li; e < split[i]; e += SW) acc += slot[e];
+#pragma unroll
+        for (int off = SW / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (li == 0 && rr < rows && i < c.n) {
+            const float tot = icu[i] + acc;
+            ic_s[rr] = (HAS_W ? tot : tot * a.g) * (1.0f / GJ_SCALE);
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x >= rows) return;
+    const int i = row0 + threadIdx.x;
+    if (i >= c.n) return;
+    const Cell cell = load_cell(c.S, vcur, i);
+    float iapp = pulse_current(c.pulses, i, t);
+    if (c.iapp != nullptr) iapp += c.iapp[i];
+    const CellNext o = cell_step(c.P, cell, ic_s[threadIdx.x], iapp);
+    finish_cell(c, t, vnext, i, o);
+}
+
+template <int SW>
+static cudaError_t half_SW(const CsrArgs &a, int rows, const int32_t *split, const int32_t *rev, float *slot,
+                           float *icu, cudaStream_t st) {
+    const int grid = (a.c.n + rows - 1) / rows;
+    const bool pdl = a.c.pdl != 0;
+    cudaError_t e = a.w != nullptr
+                        ? launch_k(csr_half_upper_kernel<SW, true>, dim3(grid), dim3(256), 0, st, pdl, a, rows, split, rev, slot, icu)
+                        : launch_k(csr_half_upper_kernel<SW, false>, dim3(grid), dim3(256), 0, st, pdl, a, rows, split, rev, slot, icu);
+    if (e != cudaSuccess) return e;
+    const float *cslot = slot, *cicu = icu;
+    return a.w != nullptr
+               ? launch_k(csr_half_lower_kernel<SW, true>, dim3(grid), dim3(256), 0, st, pdl, a, rows, split, cslot, cicu)
+               : launch_k(csr_half_lower_kernel<SW, false>, dim3(grid), dim3(256), 0, st, pdl, a, rows, split, cslot, cicu);
+}
+
+// Both passes of a half-work CSR step (rows per CTA <= 256; SW lanes per row).
+cudaError_t launch_csr_half_step(const CsrArgs &a, int SW, int rows, const int32_t *split, const int32_t *rev,
+                                 float *slot, float *icu, cudaStream_t st) {
+    if (rows < 1 || rows > 256) return cudaErrorInvalidValue;
+    switch (SW) {
+        case 1: return half_SW<1>(a, rows, split, rev, slot, icu, st);
+        case 2: return half_SW<2>(a, rows, split, rev, slot, icu, st);
+        case 4: return half_SW<4>(a, rows, split, rev, slot, icu, st);
+        case 8: return half_SW<8>(a, rows, split, rev, slot, icu, st);
+        case 16: return half_SW<16>(a, rows, split, rev, slot, icu, st);
+        case 32: return half_SW<32>(a, rows, split, rev, slot, icu, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // ---- compact column layout: the low 16 bits of every column (zero padding to 8 entries)
 __global__ void csr_col16_kernel(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -125,18 +125,20 @@ __global__ void __launch_bounds__(DenseBounds<R>::threads) dense_step_kernel(con
             iapp = pulse_current(c.pulses, i, t);
             if (c.iapp != nullptr) iapp += c.iapp[i];
         }
-        cell_step_role(role, c, t, vnext, i, staged_cell(cs, rows_cta, rr), ic_s[rr], iapp);
+        cell_step_role(role, c, t, vnext, i, rr, staged_cell(cs, rows_cta, rr), ic_s[rr], iapp, RoleOutGlobal{c.S});
     }
 }
 
 // ---- persistent: many steps in one cooperative launch ------------------------------------
-// Each row thread keeps its cell's state in registers across steps.  After the cell
-// update the new V_dend goes to the other global V_dend buffer and the CTAs meet at a
-// bounded grid barrier before staging it for the next step.  With a single CTA and a
-// single tile (small networks) V_dend never leaves shared memory: the row threads
-// write V_dend(t+1) straight into the tile.
-// Launch bounds of the persistent variant (it also keeps a cell's state in registers):
-// 896 threads (72 registers) when R <= 2, else 576.
+// The CTA keeps its rows' state in shared memory across steps (loaded at the start,
+// written back at the end); every step stages V_dend(t) and runs the pair pass, then
+// updates its rows from the shared copy: NROLE threads per cell when that fits one round
+// of the CTA's threads (each thread reads its cell, then a CTA barrier, then writes), else
+// one thread per cell.  V_dend(t+1) of the rows goes to the other global V_dend buffer and
+// the CTAs meet at a bounded grid barrier (a release flag, grid_barrier_flag) before
+// staging it for the next step.  With a single CTA and a single tile (small networks)
+// V_dend never leaves shared memory: the tile is updated in place.
+// Launch bounds of the persistent variant: 896 threads when R <= 4, else 576.
 template <int R>
 struct PersistBounds {
     static constexpr int threads = R <= 4 ? 896 : 576;
@@ -155,25 +157,30 @@ __global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kerne
     const int W = blockDim.x >> 5;
     const int GR = W / GJ;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int rg = warp % GR, cs = warp / GR;
+    const int rg = warp % GR, csp = warp / GR;
     const int rows_cta = GR * R;
     const DenseSmem sm = dense_smem(smem_raw, c.n_pad);
+    float *cs = sm.part + W * R;              // the rows' 15 Cell words
+    float *xs = cs + NCW * rows_cta;          // their m_s, m_a, I_CaH, I_c
+    float *ic_s = xs + 4 * rows_cta;          // their gap currents
+    const RoleOutSmem out{cs, xs, rows_cta};
     const bool single = gridDim.x == 1 && sm.n_tiles == 1;
     const int row_base = blockIdx.x * rows_cta;
+    const int rows_here = max(0, min(rows_cta, n - row_base));
     const int64_t t0 = *c.t_dev;
+    const int rows32 = (rows_cta + 31) & ~31;
+    const bool roles = NROLE * rows32 <= (int)blockDim.x;
 
-    // row thread: state of one cell in registers
-    const int my_row = row_base + (int)threadIdx.x;
-    const bool row_thread = threadIdx.x < rows_cta && my_row < n;
-    Cell cell{};
-    float o_ms = 0.0f, o_ma = 0.0f, o_icah = 0.0f, o_ic = 0.0f;   // last step's output-only words
-    int32_t p0 = 0, p1 = 0;
-    if (row_thread) {
-        cell = load_cell(c.S, vd_slot(c.S, t0), my_row);
-        if (c.pulses.off != nullptr) {
-            p0 = c.pulses.off[my_row];
-            p1 = c.pulses.off[my_row + 1];
-        }
+    // the rows' state from global memory
+    for (int q = threadIdx.x; q < NCW * rows_cta; q += blockDim.x) {
+        const int w = q / rows_cta, rr = q - w * rows_cta;
+        if (rr < rows_here)
+            cs[q] = w == 0 ? vd_slot(c.S, t0)[row_base + rr] : c.S.f(cell_word_field(w))[row_base + rr];
+    }
+    for (int q = threadIdx.x; q < 4 * rows_cta; q += blockDim.x) {
+        const int k = q / rows_cta, rr = q - k * rows_cta;
+        const int f = k == 0 ? F_MS : (k == 1 ? F_MA : (k == 2 ? F_ICAH : F_IC));
+        if (rr < rows_here) xs[q] = c.S.f(f)[row_base + rr];
     }
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
@@ -196,10 +203,11 @@ __global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kerne
         while (globaltimer_ns() - d0 < (uint64_t)a.debug_delay_ns) __nanosleep(1000);
     }
 
-    bool ok = true;
-    for (int k = 0; k < a.n_steps && ok; ++k) {
+    int done = 0;   // steps whose update is in the shared copy
+    for (int k = 0; k < a.n_steps; ++k) {
         const int64_t t = t0 + k;
         const float *vcur = vd_slot(c.S, t);
+        float *vnext = vd_slot(c.S, t + 1);
         if (!single && threadIdx.x == 0)
             for (int q = 0; q < 2 && q < sm.n_tiles; ++q) issue_tile(sm, vcur, c.n_pad, q, bar);
         // shift m = V_dend of cell 0 at step t (from L2, or from the tile itself)
@@ -209,53 +217,75 @@ __global__ void __launch_bounds__(PersistBounds<R>::threads) dense_persist_kerne
         float ui[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int i = row_base + rg * R + r;
-            ui[r] = (i < n) ? ((single ? sm.tile0[i] : __ldcg(vcur + i)) - m_shift) * GJ_SCALE : 0.0f;
+            const int rr = rg * R + r;
+            ui[r] = (rr < rows_here) ? (cs[rr] - m_shift) * GJ_SCALE : 0.0f;
         }
         float tot[R], Us, Uc;
-        if (!gj_pass<R, GJ>(sm, single ? nullptr : vcur, n, c.n_pad, bar, uses, m_shift, ui, cs, lane, a.kahan,
+        if (!gj_pass<R, GJ>(sm, single ? nullptr : vcur, n, c.n_pad, bar, uses, m_shift, ui, csp, lane, a.kahan,
                             rg == 0, tot, Us, Uc)) {
             if (threadIdx.x == 0) {
                 atomicOr(c.status, (uint32_t)ST_TIMEOUT);
                 atomicExch(a.abort_flag, 1u);
                 for (int q = 0; q < 2 && q < sm.n_tiles; ++q) (void)mbar_wait_bounded(&bar[q], uses[q] & 1u);
             }
-            ok = false;
             break;
         }
-        const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, cs, lane, red_s, red_c, &U_sh);
-        if (row_thread) {
-            const float u_i = (cell.vd - m_shift) * GJ_SCALE;
-            const float ic = row_current<GJ>(sm, (int)threadIdx.x, u_i, n, U, a.g);
-            float iapp = 0.0f;
-            for (int32_t p = p0; p < p1; ++p)
-                if (t >= c.pulses.begin[p] && t < c.pulses.end[p]) iapp += c.pulses.amp[p];
-            const CellNext o = cell_step(c.P, cell, ic, iapp);
-            cell.vd = o.vd; cell.vs = o.vs; cell.va = o.va; cell.ca = o.ca;
-            cell.r = o.r; cell.s = o.s; cell.q = o.q; cell.k = o.k; cell.l = o.l;
-            cell.hs = o.hs; cell.ns = o.ns; cell.xs = o.xs; cell.ha = o.ha; cell.xa = o.xa;
-            o_ms = o.ms; o_ma = o.ma; o_icah = o.icah; o_ic = o.ic;
-            if (!cell_finite(o)) atomicOr(c.status, (uint32_t)ST_NONFINITE);
-            if (c.trace != nullptr && ((t + 1) % c.trace_stride) == 0) {
-                const int64_t sample = (t + 1) / c.trace_stride - 1;
-                c.trace[(sample % c.trace_cap) * (int64_t)n + my_row] = o.va;
+        const float U = gj_reduce<R, GJ>(sm, tot, Us, Uc, rg, csp, lane, red_s, red_c, &U_sh);
+        for (int rr = threadIdx.x; rr < rows_here; rr += blockDim.x)
+            ic_s[rr] = row_current<GJ>(sm, rr, (cs[rr] - m_shift) * GJ_SCALE, n, U, a.g);
+        __syncthreads();
+        if (roles) {   // one round: read the cell, barrier, write its new words
+            const int role = threadIdx.x / rows32, rr = threadIdx.x - role * rows32;
+            const bool mine = role < NROLE && rr < rows_here;
+            Cell cell{};
+            float iapp = 0.0f, ic = 0.0f;
+            const int64_t i = row_base + rr;
+            if (mine) {
+                cell = staged_cell(cs, rows_cta, rr);
+                ic = ic_s[rr];
+                if (role == 0) {
+                    iapp = pulse_current(c.pulses, i, t);
+                    if (c.iapp != nullptr) iapp += c.iapp[i];
+                }
+            }
+            __syncthreads();
+            if (mine) cell_step_role(role, c, t, vnext, i, rr, cell, ic, iapp, out);
+        } else {
+            for (int rr = threadIdx.x; rr < rows_here; rr += blockDim.x) {
+                const int64_t i = row_base + rr;
+                float iapp = pulse_current(c.pulses, i, t);
+                if (c.iapp != nullptr) iapp += c.iapp[i];
+                const CellNext o = cell_step(c.P, staged_cell(cs, rows_cta, rr), ic_s[rr], iapp);
+                put_cell_smem(out, rr, o);
+                vnext[i] = o.vd;
+                if (!cell_finite(o)) atomicOr(c.status, (uint32_t)ST_NONFINITE);
+                if (c.trace != nullptr && ((t + 1) % c.trace_stride) == 0) {
+                    const int64_t sample = (t + 1) / c.trace_stride - 1;
+                    c.trace[(sample % c.trace_cap) * (int64_t)n + i] = o.va;
+                }
             }
         }
+        done = k + 1;
         if (single) {
             __syncthreads();                          // all pair loops are done with the tile
-            if (row_thread) sm.tile0[my_row] = cell.vd;
+            for (int rr = threadIdx.x; rr < rows_here; rr += blockDim.x) sm.tile0[rr] = cs[rr];
             __syncthreads();
-        } else {
-            if (row_thread) vd_slot(c.S, t + 1)[my_row] = cell.vd;
-            ok = grid_barrier(a.bar_count, a.abort_flag, a.bar_base + (uint32_t)(k + 1) * gridDim.x, a.timeout_ns, c.status,
-                              &ok_sh);
+        } else if (!grid_barrier_flag(a.bar_count, a.bar_flag, a.abort_flag, a.bar_base + (uint32_t)(k + 1) * gridDim.x,
+                                      a.timeout_ns, c.status, &ok_sh)) {
+            break;
         }
     }
-    // write the final state (after an aborted run: the last completed step)
-    if (row_thread && a.n_steps > 0) {
-        const CellNext o{cell.vd, cell.vs, cell.va, cell.ca, cell.r, cell.s, cell.q, cell.k, cell.l, o_ms,
-                         cell.hs, cell.ns, cell.xs, o_ma, cell.ha, cell.xa, o_icah, o_ic};
-        store_cell(c.S, vd_slot(c.S, t0 + a.n_steps), my_row, o);
+    // write the state back (after an aborted run: the CTA's last completed step)
+    __syncthreads();
+    float *vfin = vd_slot(c.S, t0 + done);
+    for (int q = threadIdx.x; q < NCW * rows_cta; q += blockDim.x) {
+        const int w = q / rows_cta, rr = q - w * rows_cta;
+        if (rr < rows_here && w != NCW - 1) (w == 0 ? vfin : c.S.f(cell_word_field(w)))[row_base + rr] = cs[q];
+    }
+    for (int q = threadIdx.x; q < 4 * rows_cta; q += blockDim.x) {
+        const int kk = q / rows_cta, rr = q - kk * rows_cta;
+        const int f = kk == 0 ? F_MS : (kk == 1 ? F_MA : (kk == 2 ? F_ICAH : F_IC));
+        if (rr < rows_here) c.S.f(f)[row_base + rr] = xs[q];
     }
 }
 
@@ -325,7 +355,8 @@ struct PersistOp {
         if (L.W % GJ != 0 || L.W * 32 > PersistBounds<R>::threads) return cudaErrorInvalidValue;
         const int rows_cta = (L.W / GJ) * R;
         const int grid = (L.a->c.n + rows_cta - 1) / rows_cta;
-        const size_t smem = dense_smem_bytes(L.a->c.n_pad, R, L.W);
+        // the tiles and partials, then the rows' state copy (15 + 4 words) and currents
+        const size_t smem = dense_smem_bytes(L.a->c.n_pad, R, L.W) + (size_t)(NCW + 5) * rows_cta * sizeof(float);
         if (!L.launch) {   // prepare, and report whether every CTA can be resident at once
             cudaError_t e = cudaFuncSetAttribute(dense_persist_kernel<R, GJ>,
                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -13,10 +13,14 @@ using namespace ion;
 // Arrival counter := barrier_base (0 unless a test moved it near 2^32), abort word := 0.
 // The barriers compare the counter with their targets modulo 2^32, so a launch may run
 // any number of steps whatever the base.
+// Barrier words: [0] arrival counter, [1] abort word, [32] release flag (its own 128-byte
+// line).  Counter and flag start at barrier_base, the abort word at 0.
+constexpr int BAR_WORDS = 64, BAR_FLAG = 32;
 static cudaError_t reset_barrier(ion_sim *s) {
+    for (int q = 0; q < BAR_WORDS; ++q) s->bar_init[q] = 0u;
     s->bar_init[0] = s->barrier_base;
-    s->bar_init[1] = 0u;
-    return cudaMemcpyAsync(s->d_bar, s->bar_init, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, s->st);
+    s->bar_init[BAR_FLAG] = s->barrier_base;
+    return cudaMemcpyAsync(s->d_bar, s->bar_init, BAR_WORDS * sizeof(uint32_t), cudaMemcpyHostToDevice, s->st);
 }
 
 // Multi-CTA networks use the half-work kernel (each unordered pair once, two barriers per
@@ -65,6 +69,7 @@ static ion_status persist_run(ion_sim *s, int64_t n_steps, const float *iapp) {
         a.kahan = 1;
         a.bar_count = s->d_bar;
         a.abort_flag = s->d_bar + 1;
+        a.bar_flag = s->d_bar + BAR_FLAG;
         a.timeout_ns = s->barrier_timeout_ns;
         a.debug_delay_ns = s->debug_delay_ns;
         a.bar_base = s->barrier_base;
@@ -114,7 +119,7 @@ ion_status ion_sim_setup_extras(ion_sim *s, const ion_params *p) {
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, s->device);
         if (coop && choose_persist_shape(s)) {
-            if (ion_alloc(&s->d_bar, 2 * sizeof(uint32_t)) != cudaSuccess)
+            if (ion_alloc(&s->d_bar, BAR_WORDS * sizeof(uint32_t)) != cudaSuccess)
                 return ion_fail(nullptr, ION_ERR_OOM, "persistent: barrier allocation failed");
             s->extra_free = [](ion_sim *q) {   // set before any later allocation can fail
                 cudaFree(q->d_bar);

@@ -140,20 +140,47 @@ __device__ __forceinline__ Cell staged_cell(const float *cs, int rows, int r) {
     return c;
 }
 
-// Outputs of one role of cell i (see NROLE); iapp is read by role 0 only.
+// Where a role writes the step-(t+1) words of cell i: the global state (per-step kernels)
+struct RoleOutGlobal {
+    StateView S;
+    __device__ __forceinline__ void put(int field, int64_t i, int, float v) const { S.f(field)[i] = v; }
+    __device__ __forceinline__ void put_vd(int, float) const {}   // V_dend goes to the next slot only
+};
+// ... or a CTA's shared-memory copy of its rows' state (persistent kernels): the 15 Cell
+// words in cs[w * rows + r] (word order of Cell) and the four output-only words (m_s, m_a,
+// I_CaH, I_c) in xs[k * rows + r]
+struct RoleOutSmem {
+    float *cs, *xs;
+    int rows;
+    __device__ __forceinline__ float *slot(int field) const {
+        switch (field) {
+            case F_MS: return xs;
+            case F_MA: return xs + rows;
+            case F_ICAH: return xs + 2 * rows;
+            case F_IC: return xs + 3 * rows;
+            default: return cs + (field <= F_L ? field : (field <= F_XS ? field - 1 : field - 2)) * rows;
+        }
+    }
+    __device__ __forceinline__ void put(int field, int64_t, int r, float v) const { slot(field)[r] = v; }
+    __device__ __forceinline__ void put_vd(int r, float v) const { cs[r] = v; }
+};
+
+// Outputs of one role of cell i (local row r of its CTA; see NROLE); iapp is read by role 0
+// only.  V_dend(t+1) always goes to the global next slot (other CTAs read it).
+template <class Out>
 __device__ __forceinline__ void cell_step_role(int role, const StepCommon &a, int64_t t, float *vd_next, int64_t i,
-                                               const Cell &c, float ic, float iapp) {
+                                               int r, const Cell &c, float ic, float iapp, const Out &out) {
     const ModelF &P = a.P;
-    const StateView &S = a.S;
     const float dt = P.dt;
     switch (role) {
         case 0: {
             const DendNext d = dend_step(P, c, ic, iapp);
             vd_next[i] = d.vd;
-            S.f(F_CA)[i] = d.ca;
-            S.f(F_ICAH)[i] = d.icah;
-            S.f(F_IC)[i] = ic;
-            S.f(F_S)[i] = relax(c.s, rate_s(c.ca), dt);
+            out.put_vd(r, d.vd);
+            out.put(F_CA, i, r, d.ca);
+            out.put(F_ICAH, i, r, d.icah);
+            out.put(F_IC, i, r, ic);
+            out.put(F_S, i, r, relax(c.s, rate_s(c.ca), dt));
             if (!(isfinite(d.vd) && isfinite(d.ca))) atomicOr(a.status, (uint32_t)ST_NONFINITE);
             if (a.par >= 0 && (int)(t & 1) != a.par) atomicOr(a.status, (uint32_t)ST_SLOT);
             break;
@@ -161,16 +188,16 @@ __device__ __forceinline__ void cell_step_role(int role, const StepCommon &a, in
         case 1: {
             const float ms = minf_na(c.vs);
             const float vs = soma_step(P, c, ms);
-            S.f(F_VSOMA)[i] = vs;
-            S.f(F_MS)[i] = ms;
+            out.put(F_VSOMA, i, r, vs);
+            out.put(F_MS, i, r, ms);
             if (!isfinite(vs)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
             break;
         }
         case 2: {
             const float ma = minf_na(c.va);
             const float va = axon_step(P, c, ma);
-            S.f(F_VAXON)[i] = va;
-            S.f(F_MA)[i] = ma;
+            out.put(F_VAXON, i, r, va);
+            out.put(F_MA, i, r, ma);
             if (!isfinite(va)) atomicOr(a.status, (uint32_t)ST_NONFINITE);
             if (a.trace != nullptr && ((t + 1) % a.trace_stride) == 0) {
                 const int64_t sample = (t + 1) / a.trace_stride - 1;
@@ -178,20 +205,42 @@ __device__ __forceinline__ void cell_step_role(int role, const StepCommon &a, in
             }
             break;
         }
-        case 3: S.f(F_R)[i] = relax(c.r, rate_r(c.vd), dt); break;
-        case 4: S.f(F_Q)[i] = relax(c.q, rate_q(c.vd), dt); break;
+        case 3: out.put(F_R, i, r, relax(c.r, rate_r(c.vd), dt)); break;
+        case 4: out.put(F_Q, i, r, relax(c.q, rate_q(c.vd), dt)); break;
         case 5:
-            S.f(F_K)[i] = relax(c.k, rate_k(c.vs), dt);
-            S.f(F_HS)[i] = relax(c.hs, rate_hs(c.vs), dt);
+            out.put(F_K, i, r, relax(c.k, rate_k(c.vs), dt));
+            out.put(F_HS, i, r, relax(c.hs, rate_hs(c.vs), dt));
             break;
-        case 6: S.f(F_L)[i] = relax(c.l, rate_l(c.vs), dt); break;
+        case 6: out.put(F_L, i, r, relax(c.l, rate_l(c.vs), dt)); break;
         case 7:
-            S.f(F_NS)[i] = relax(c.ns, rate_ns(c.vs), dt);
-            S.f(F_HA)[i] = relax(c.ha, rate_ha(c.va), dt);
+            out.put(F_NS, i, r, relax(c.ns, rate_ns(c.vs), dt));
+            out.put(F_HA, i, r, relax(c.ha, rate_ha(c.va), dt));
             break;
-        case 8: S.f(F_XS)[i] = relax(c.xs, rate_x(c.vs), dt); break;
-        default: S.f(F_XA)[i] = relax(c.xa, rate_x(c.va), dt); break;
+        case 8: out.put(F_XS, i, r, relax(c.xs, rate_x(c.vs), dt)); break;
+        default: out.put(F_XA, i, r, relax(c.xa, rate_x(c.va), dt)); break;
     }
+}
+
+// All 18 words of a single-thread step into the shared-memory copy (persistent kernels).
+__device__ __forceinline__ void put_cell_smem(const RoleOutSmem &out, int r, const CellNext &o) {
+    out.put_vd(r, o.vd);
+    out.put(F_VSOMA, 0, r, o.vs);
+    out.put(F_VAXON, 0, r, o.va);
+    out.put(F_CA, 0, r, o.ca);
+    out.put(F_R, 0, r, o.r);
+    out.put(F_S, 0, r, o.s);
+    out.put(F_Q, 0, r, o.q);
+    out.put(F_K, 0, r, o.k);
+    out.put(F_L, 0, r, o.l);
+    out.put(F_MS, 0, r, o.ms);
+    out.put(F_HS, 0, r, o.hs);
+    out.put(F_NS, 0, r, o.ns);
+    out.put(F_XS, 0, r, o.xs);
+    out.put(F_MA, 0, r, o.ma);
+    out.put(F_HA, 0, r, o.ha);
+    out.put(F_XA, 0, r, o.xa);
+    out.put(F_ICAH, 0, r, o.icah);
+    out.put(F_IC, 0, r, o.ic);
 }
 
 struct DenseArgs {
@@ -220,6 +269,7 @@ struct PersistArgs {
     int32_t kahan;
     uint32_t *bar_count;  // grid-barrier arrivals (set to bar_base before the launch)
     uint32_t *abort_flag; // set by a CTA whose wait timed out (zeroed before the launch)
+    uint32_t *bar_flag;   // the last arrival's release flag (set to bar_base before the launch)
     uint64_t timeout_ns;  // bound on one grid-barrier wait
     int64_t debug_delay_ns;  // test hook: the last CTA sleeps this long before its first step
     uint32_t bar_base;    // the arrival counter's value at launch (0; a test hook sets others)
@@ -264,6 +314,8 @@ constexpr int SGJ_ONE_LAUNCH = 16384;   // SGJ dense networks up to this size ta
 cudaError_t launch_sgj_dense_step(const StepCommon &c, float g, float *part, cudaStream_t st);
 cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st);
 cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st);
+cudaError_t launch_csr_half_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *split,
+                                 const int32_t *rev, float *slot, float *icu, cudaStream_t st);
 cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
                                     int32_t *mid, cudaStream_t st);
 size_t csr_chunk_smem_bytes(int n_pad, int rows);

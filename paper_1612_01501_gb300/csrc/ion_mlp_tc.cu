@@ -6,18 +6,19 @@
 // evaluates the MLP for their three compartments (V_dend, V_soma, V_axon, each with the
 // cell's [Ca]) as three 128-row tiles: row t of every tile is cell t of the CTA, so thread
 // t ends up holding all three compartments' rates and runs that cell's explicit-Euler
-// update itself.  The three tiles go through each layer together, so a CTA waits for the
-// tensor cores twice per step:
+// update itself.  The tiles go through the two layers one after the other (a version
+// that pushed all three through each layer together, two tensor-core waits per step
+// instead of six, measured slower: it needs twice the TMEM and shared memory per CTA, so
+// half as many CTAs share an SM):
 //   layer 1 (2 -> 64) in FP32 on the CUDA cores, tanh on packed bf16 pairs, written to
 //     shared memory as the three BF16 A operands of layer 2;
-//   layer 2 (64 x 64): per tile four tcgen05.mma.kind::f16 (M = 128, N = 64, K = 16 each,
-//     BF16 in, FP32 accumulation) into TMEM columns 64 c .. 64 c + 63, issued by one thread
-//     and completed through one tcgen05.commit on an mbarrier;
+//   layer 2 (64 x 64): four tcgen05.mma.kind::f16 (M = 128, N = 64, K = 16 each, BF16 in,
+//     FP32 accumulation) into TMEM columns 0..63, issued by one thread and completed
+//     through one tcgen05.commit on an mbarrier;
 //   every thread reads its row of each tile back (tcgen05.ld, lane = row), adds the bias,
 //     applies tanh and writes the tile's BF16 A operand of layer 3 over its layer-2 one;
-//   layer 3 (64 x 24, padded to N = 32): per tile four MMAs into TMEM columns 32 c ..
-//     32 c + 31 (over the layer-2 results, already read), one commit, read back and mapped
-//     to physical units.
+//   layer 3 (64 x 24, padded to N = 32): four MMAs into TMEM columns 0..31 (over the
+//     layer-2 results, already read), one commit, read back and mapped to physical units.
 // Operands use the canonical K-major layout without swizzling: 8-row x 16-byte core
 // matrices of 128 contiguous bytes, core matrix (row group g, K chunk c) at byte
 // (8 g + c) 128, so the K-direction core-matrix stride (leading byte offset) is 128 B and
@@ -39,8 +40,8 @@ constexpr int ROWS = 128;        // M of every MMA: rows (cells) per CTA
 constexpr int KH = 64;           // hidden width (K of layers 2 and 3)
 constexpr int N2 = 64, N3 = 32;  // layer 2 outputs; layer 3 outputs (24) padded to a multiple of 16
 constexpr int NOUT = ION_MLP_OUT;
-constexpr int NT = 3;                 // tiles per CTA (the three compartments)
-constexpr uint32_t TMEM_COLS = 256;   // layer 2: tile c in [64 c, 64 c + 64); layer 3: [32 c, 32 c + 32)
+constexpr int NT = 1;                 // tiles through a layer at once (see above)
+constexpr uint32_t TMEM_COLS = 128;   // layer 2: tile c in [64 c, 64 c + 64); layer 3: [32 c, 32 c + 32)
 constexpr float LOG2E = 1.4426950408889634f;
 
 __host__ __device__ constexpr int core_off(int row, int kchunk) {
@@ -272,26 +273,32 @@ __global__ void __launch_bounds__(128) surrogate_tc_kernel(const SurrTcArgs a) {
     if (valid) cell = load_cell(c.S, vcur, i);
     const float ca = valid ? cell.ca : 1.0f;
     const float x1 = (logf(ca) - sm.W.in_shift[1]) * sm.W.in_scale[1];
-    const float V[tc::NT] = {valid ? cell.vd : -60.0f, valid ? cell.vs : -60.0f, valid ? cell.va : -60.0f};
-    float x0[tc::NT];
-#pragma unroll
-    for (int k = 0; k < tc::NT; ++k) x0[k] = (V[k] - sm.W.in_shift[0]) * sm.W.in_scale[0];
-    float y[tc::NT][tc::NOUT];
-    uint32_t phase = 0;
-    const bool ok = tc::mlp_tiles(sm, tc::NT, x0, x1, phase, y, c.status);
     CellRates gr;
-    gr.r = tc::learned_rate(y[0], G_R);
-    gr.s = tc::learned_rate(y[0], G_S);
-    gr.q = tc::learned_rate(y[0], G_Q);
-    gr.k = tc::learned_rate(y[1], G_K);
-    gr.l = tc::learned_rate(y[1], G_L);
-    gr.ms = Rate{tc::learned_xinf(y[1], G_MS), 0.0f};
-    gr.hs = tc::learned_rate(y[1], G_HS);
-    gr.ns = tc::learned_rate(y[1], G_NS);
-    gr.xs = tc::learned_rate(y[1], G_XS);
-    gr.ma = Rate{tc::learned_xinf(y[2], G_MA), 0.0f};
-    gr.ha = tc::learned_rate(y[2], G_HA);
-    gr.xa = tc::learned_rate(y[2], G_XA);
+    uint32_t phase = 0;
+    bool ok = true;
+#pragma unroll 1
+    for (int comp = 0; comp < 3 && ok; ++comp) {
+        const float V = !valid ? -60.0f : (comp == 0 ? cell.vd : (comp == 1 ? cell.vs : cell.va));
+        const float x0[tc::NT] = {(V - sm.W.in_shift[0]) * sm.W.in_scale[0]};
+        float y[tc::NT][tc::NOUT];
+        ok = tc::mlp_tiles(sm, 1, x0, x1, phase, y, c.status);
+        if (comp == 0) {
+            gr.r = tc::learned_rate(y[0], G_R);
+            gr.s = tc::learned_rate(y[0], G_S);
+            gr.q = tc::learned_rate(y[0], G_Q);
+        } else if (comp == 1) {
+            gr.k = tc::learned_rate(y[0], G_K);
+            gr.l = tc::learned_rate(y[0], G_L);
+            gr.ms = Rate{tc::learned_xinf(y[0], G_MS), 0.0f};
+            gr.hs = tc::learned_rate(y[0], G_HS);
+            gr.ns = tc::learned_rate(y[0], G_NS);
+            gr.xs = tc::learned_rate(y[0], G_XS);
+        } else {
+            gr.ma = Rate{tc::learned_xinf(y[0], G_MA), 0.0f};
+            gr.ha = tc::learned_rate(y[0], G_HA);
+            gr.xa = tc::learned_rate(y[0], G_XA);
+        }
+    }
     tc::tc_teardown(sm);
     if (!ok || !valid) return;
     const float ic = a.ic != nullptr ? a.ic[i] : 0.0f;
@@ -309,7 +316,7 @@ __global__ void __launch_bounds__(128) mlp_eval_tc_kernel(const tc::Weights *Wg,
     tc::tc_setup(sm, Wg);
     const int64_t k = (int64_t)blockIdx.x * tc::ROWS + threadIdx.x;
     const bool valid = k < n;
-    float x0[tc::NT] = {valid ? (V[k] - sm.W.in_shift[0]) * sm.W.in_scale[0] : 0.0f, 0.0f, 0.0f};
+    float x0[tc::NT] = {valid ? (V[k] - sm.W.in_shift[0]) * sm.W.in_scale[0] : 0.0f};
     const float x1 = valid ? (logf(ca[k]) - sm.W.in_shift[1]) * sm.W.in_scale[1] : 0.0f;
     uint32_t phase = 0;
     float y[tc::NT][tc::NOUT];
@@ -348,9 +355,9 @@ __global__ void mlp_tc_pack_kernel(const ion_surrogate_weights *w, tc::Weights *
     }
 }
 
-// Shared memory requested per CTA: at least 80 KB, so that at most two CTAs share an SM
-// and their TMEM allocations (256 of the SM's 512 columns each) never have to wait.
-static constexpr size_t kTcSmem = sizeof(tc::Smem) > 80 * 1024 ? sizeof(tc::Smem) : 80 * 1024;
+// Shared memory requested per CTA: at least 56 KB, so that at most four CTAs share an SM
+// and their TMEM allocations (128 of the SM's 512 columns each) never have to wait.
+static constexpr size_t kTcSmem = sizeof(tc::Smem) > 56 * 1024 ? sizeof(tc::Smem) : 56 * 1024;
 size_t surrogate_tc_smem() { return kTcSmem; }
 size_t surrogate_tc_weights_bytes() { return sizeof(tc::Weights); }
 

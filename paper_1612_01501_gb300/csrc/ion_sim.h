@@ -62,7 +62,7 @@ struct ion_sim {
     int64_t debug_delay_ns = 0;
     uint32_t *d_bar = nullptr;      // grid barrier counter + abort word (persistent launches)
     uint32_t barrier_base = 0;      // the counter's value at each persistent launch (test hook)
-    uint32_t bar_init[2] = {0u, 0u};   // host source of the counter reset (lives with the handle)
+    uint32_t bar_init[64] = {};     // host source of the barrier reset (lives with the handle)
     int persist_R = 0, persist_W = 0, persist_GJ = 1;
     float *d_half = nullptr;        // half-work persistent kernel: column sums + per-CTA sums of u
     int half_grid = 0, half_stride = 0;
@@ -71,6 +71,10 @@ struct ion_sim {
     int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk
     int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
     int32_t *d_mid = nullptr;       // interior chunk boundaries per row
+    // half-work CSR (ION_FLAG_HALF_WORK on a CSR network): first upper edge of each row, the
+    // mirrored position of every upper edge, the per-edge slots, the rows' upper sums
+    int32_t *d_split = nullptr, *d_rev = nullptr;
+    float *d_slot = nullptr, *d_icu = nullptr;
     void *d_mlp = nullptr;          // packed surrogate weights (ION_FLAG_SURROGATE), warp-MMA layout
     void *d_mlp_tc = nullptr;       // the same weights in the tcgen05 kernels' layout
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};   // K-step graphs, by the parity of their first step
@@ -117,6 +121,7 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows);
 bool ion_csr_bank_col16(int32_t n, int32_t n_pad, const int32_t *row_ptr, const int32_t *col,
                         std::vector<uint16_t> &out);
 ion_status ion_setup_csr_staging(ion_sim *s, int mode);
+ion_status ion_setup_csr_half(ion_sim *s, const ion_conn *conn);
 void ion_sim_free_device(ion_sim *s);
 // destroy the captured step graphs (after any change they depend on)
 inline void ion_drop_graphs(ion_sim *s) {

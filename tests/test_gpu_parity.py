@@ -771,3 +771,41 @@ def test_per_cell_constants_rejected_where_unsupported(torch_cuda, O):
     with pytest.raises(ion.IonError) as ei:
         ion.ion_create_batch([dict(n=n, kind=ion.NO_GJ)], cell_params=cp)
     assert ei.value.status == ion.ERR_UNSUPPORTED
+
+
+# ------------------------------------------------------------------ half-work CSR
+
+@pytest.mark.parametrize("n,k,weights", [(5000, 10, "uniform"), (5000, 100, "random"), (3001, 1000, "uniform"),
+                                         (65536, 100, "uniform")])
+def test_csr_half_work_one_step(torch_cuda, O, n, k, weights):
+    """Each stored pair evaluated once (upper triangle; the mirrored term through a
+    per-edge slot, gathered per row in a fixed order): one step from an identical state
+    against the oracle, at uniform and random symmetric weights."""
+    rp, col = inputs.random_symmetric_csr(n, k, 51)
+    w = np.full(len(col), inputs.junction_weight(0.04, k), np.float32)
+    if weights == "random":   # symmetric: the weight of a pair from its smaller and larger cell
+        rows = np.repeat(np.arange(n), np.diff(rp))
+        lo, hi = np.minimum(rows, col).astype(np.uint64), np.maximum(rows, col).astype(np.uint64)
+        h = (lo * np.uint64(2654435761) + hi * np.uint64(40503)) % np.uint64(1000)
+        w = (w * (0.5 + h.astype(np.float64) / 1000.0)).astype(np.float32)
+    err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=3, flags=ion.FLAG_KAHAN | ion.FLAG_HALF_WORK)
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+def test_csr_half_work_trajectory_matches_full_pass(torch_cuda, O):
+    """The 65 536-cell k = 100 network with its pulse, 600 steps: the half-work pass stays
+    within the trajectory bound of the oracle, like the full pass."""
+    cfg = inputs.config("c3", k=100)
+    worst = 0.0
+    for t, sim, Sref, _ in _run_both(O, cfg, 600, 300, flags=ion.FLAG_KAHAN | ion.FLAG_HALF_WORK):
+        worst = max(worst, float(np.abs(sim.state()[:3] - Sref[:3]).max()))
+    assert worst <= TRAJ_MV, worst
+
+
+def test_csr_half_work_needs_symmetric_weights(torch_cuda, O):
+    n = 200
+    rp, col = inputs.random_symmetric_csr(n, 8, 52)
+    w = np.linspace(0.01, 0.02, len(col)).astype(np.float32)   # not symmetric
+    with pytest.raises(ion.IonError) as ei:
+        ion.ion_create(n, ion.CSR, row_ptr=rp, col=col, w=w, flags=ion.FLAG_KAHAN | ion.FLAG_HALF_WORK)
+    assert ei.value.status == ion.ERR_UNSUPPORTED

@@ -219,8 +219,8 @@ def test_learned_rates_spiking(trained, O):
 
 def test_surrogate_gain_is_reported(trained, O):
     """What the learned rate functions gain on this GPU: both paths time the same 4096-cell
-    network (the ratio is printed; the exact rate functions are cheap on the SFU, so the
-    surrogate is not expected to be faster here)."""
+    network.  The exact rate functions are cheap on the SFU, so the surrogate is slower
+    here; the test holds the ratio to the stated floor."""
     import time
     w, _ = trained
     n = 4096
@@ -240,6 +240,9 @@ def test_surrogate_gain_is_reported(trained, O):
             sim.sync()
             rate[name] = n * 2000 / (time.perf_counter() - t0)
             assert np.all(np.isfinite(sim.state()))
-    print(f"cell-steps/s: exact {rate['exact']:.3e}, surrogate {rate['surrogate']:.3e}, "
-          f"gain {rate['surrogate'] / rate['exact']:.2f}x")
-    assert rate["exact"] > 0 and rate["surrogate"] > 0
+    gain = rate["surrogate"] / rate["exact"]
+    print(f"cell-steps/s: exact {rate['exact']:.3e}, surrogate {rate['surrogate']:.3e}, gain {gain:.2f}x")
+    # the stated result on this GPU: the learned rates cost about twice the exact ones
+    # (0.46-0.49x measured on the full C5 network: 192 tanh.bf16x2 per cell-step against
+    # ~36 SFU operations); this guards against a regression beyond that
+    assert gain >= 0.3, gain
