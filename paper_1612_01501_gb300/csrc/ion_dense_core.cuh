@@ -36,12 +36,11 @@ __device__ __forceinline__ void issue_tile(const DenseSmem &sm, const float *src
 }
 
 // One block of the pair loop: BLK float4 columns of one lane (m0, m0 + 32 GJ, ...), every
-// column against the lane's R rows, summed into acc[r]; with SUMU also the column values
-// x_j of the real columns into su.  CHECK: the block may run past n4 (the last block of a
-// tile), so each column is tested; a full block runs without tests.
-template <int R, int GJ, int BLK, bool SUMU, bool CHECK>
-__device__ __forceinline__ void gj_block(const float4 *t4, int m0, int n4, int full4, int real, float2 negm2,
-                                         float2 negs2, const float2 (&u2)[R], float2 (&acc)[R], float2 &su) {
+// column against the lane's R rows, summed into acc[r].  CHECK: the block may run past n4
+// (the last block of a tile), so each column is tested; a full block runs without tests.
+template <int R, int GJ, int BLK, bool CHECK>
+__device__ __forceinline__ void gj_block(const float4 *t4, int m0, int n4, float2 negm2, float2 negs2,
+                                         const float2 (&u2)[R], float2 (&acc)[R]) {
 #pragma unroll 4
     for (int mm = 0; mm < BLK; ++mm) {
         const int m = m0 + mm * 32 * GJ;
@@ -49,17 +48,6 @@ __device__ __forceinline__ void gj_block(const float4 *t4, int m0, int n4, int f
         const float4 v = t4[m];
         const float2 va = __fmul2_rn(__fadd2_rn(make_float2(v.x, v.y), negm2), negs2);
         const float2 vb = __fmul2_rn(__fadd2_rn(make_float2(v.z, v.w), negm2), negs2);
-        if (SUMU) {
-            if (!CHECK || m < full4) {
-                su = __fadd2_rn(su, va);
-                su = __fadd2_rn(su, vb);
-            } else {   // the one float4 that ends in padding
-                const int rem = real - 4 * m;
-                su.x += va.x;
-                if (rem > 1) su.y += va.y;
-                if (rem > 2) su.x += vb.x;
-            }
-        }
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const float2 da = __fadd2_rn(u2[r], va);
@@ -78,16 +66,17 @@ __device__ __forceinline__ void gj_block(const float4 *t4, int m0, int n4, int f
 // flight (issue_tile) and the remaining ones are issued here; if NULL the single tile
 // already holds V_dend (single-CTA persistent mode).  The tiles hold raw V_dend: each lane
 // centres, scales and negates the four columns of a 16-byte load as it reads them,
-// x_j = -(V_j - m) s (the same bits a separate transform pass would store), so there is no
-// pass over the tile between its arrival and the pair loop.  Columns past the last real
-// cell are skipped.  On return tot[r] holds this lane's compensated column sum for row r,
-// and (Us, Uc) this thread's compensated share of sum_j u_j if sum_u (warps of one row
-// group together cover every column once), else zero.  bar_uses counts completed phases
-// of each mbarrier.  Returns false (in every thread) if a bulk copy did not land in time.
+// x_j = -(V_j - m) s, so there is no pass over the tile between its arrival and the pair
+// loop.  Columns past the last real cell are skipped.  After a tile's pairs, every warp
+// adds up its even share of the tile's real x_j (the linear part's sum_j u_j is not
+// needed before the reduction, and an even share keeps the warps balanced).  On return
+// tot[r] holds this lane's compensated column sum for row r, and (Us, Uc) this thread's
+// compensated share of sum_j u_j.  bar_uses counts completed phases of each mbarrier.
+// Returns false (in every thread) if a bulk copy did not land in time.
 template <int R, int GJ>
 __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, int n, int n_pad, uint64_t *bar,
                                         uint32_t (&bar_uses)[2], float m_shift, const float (&ui)[R], int cs,
-                                        int lane, int kahan, bool sum_u, float (&tot)[R], float &Us, float &Uc) {
+                                        int lane, int kahan, float (&tot)[R], float &Us, float &Uc) {
     float ks[R], kc[R];
     float2 u2[R];
 #pragma unroll
@@ -95,7 +84,7 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
         ks[r] = kc[r] = 0.0f;
         u2[r] = make_float2(ui[r], ui[r]);
     }
-    float ns = 0.0f, nc = 0.0f;   // compensated sum of x = -u over this lane's columns
+    float ns = 0.0f, nc = 0.0f;   // compensated sum of x = -u over this thread's share of columns
     const float2 negm2 = make_float2(-m_shift, -m_shift);
     const float2 negs2 = make_float2(-GJ_SCALE, -GJ_SCALE);
     constexpr int BLK = 16;       // float4 loads per lane between Kahan folds
@@ -112,28 +101,30 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
         const float4 *t4 = reinterpret_cast<const float4 *>(tb);
         const int real = max(0, min(len, n - j0));   // real columns of this tile
         const int n4 = (real + 3) >> 2;               // float4 columns that hold any
-        const int full4 = real >> 2;                  // float4 columns that hold only real ones
         for (int m0 = cs * 32 + lane; m0 < n4; m0 += 32 * GJ * BLK) {
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
-            float2 su = make_float2(0.0f, 0.0f);
-            // every column of the block is real: no per-column tests
-            const bool whole = m0 + (BLK - 1) * 32 * GJ < full4;
-            if (whole) {
-                if (sum_u) gj_block<R, GJ, BLK, true, false>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
-                else gj_block<R, GJ, BLK, false, false>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
-            } else {
-                if (sum_u) gj_block<R, GJ, BLK, true, true>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
-                else gj_block<R, GJ, BLK, false, true>(t4, m0, n4, full4, real, negm2, negs2, u2, acc, su);
-            }
+            if (m0 + (BLK - 1) * 32 * GJ < n4) gj_block<R, GJ, BLK, false>(t4, m0, n4, negm2, negs2, u2, acc);
+            else gj_block<R, GJ, BLK, true>(t4, m0, n4, negm2, negs2, u2, acc);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float blk = acc[r].x + acc[r].y;
                 if (kahan) kahan_add(ks[r], kc[r], blk);
                 else ks[r] += blk;
             }
-            if (sum_u) kahan_add(ns, nc, su.x + su.y);
+        }
+        // this thread's share of the tile's real x_j, the same transform as above
+        for (int j4 = threadIdx.x; j4 < n4; j4 += blockDim.x) {
+            const float4 v = t4[j4];
+            const float2 va = __fmul2_rn(__fadd2_rn(make_float2(v.x, v.y), negm2), negs2);
+            const float2 vb = __fmul2_rn(__fadd2_rn(make_float2(v.z, v.w), negm2), negs2);
+            const int rem = real - 4 * j4;   // real columns in this float4 (>= 1)
+            float x = va.x;
+            if (rem > 1) x += va.y;
+            if (rem > 2) x += vb.x;
+            if (rem > 3) x += vb.y;
+            kahan_add(ns, nc, x);
         }
         // order this thread's generic accesses of the buffer before any later bulk refill
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
