@@ -52,7 +52,6 @@ struct BatchArgs {
     const uint16_t *col16;    // network-local columns (TILE_C16 networks)
     const float *w;
     int32_t kahan;
-    int32_t stage_off;        // byte offset of the cell-word stage in dynamic shared memory
 };
 
 // V_dend of a network-local column from shared memory (the network's staged copy)
@@ -156,9 +155,6 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
     const float *vcur = vd_cur(c);
     float *vnext = vd_next(c);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the tile's rows' state words travel to shared memory while the gap currents are summed
-    float *cs = reinterpret_cast<float *>(smem_raw + a.stage_off);
-    stage_cells(cs, c.S, vcur, T.row0, T.rows, c.n);
 
     if (T.kind == TILE_DENSE) {
         const DenseSmem sm = dense_smem(smem_raw, T.n_pad);   // one tile: n_pad <= 8192
@@ -185,7 +181,6 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
                 atomicOr(c.status, (uint32_t)ST_TIMEOUT);
                 (void)mbar_wait_bounded(&bar[0], uses[0] & 1u);
             }
-            cp_async_wait_all();
             return;
         }
         const float U = gj_reduce<R, 1>(sm, tot, Us, Uc, warp, 0, lane, red_s, red_c, &U_sh);
@@ -209,7 +204,6 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
                 atomicOr(c.status, (uint32_t)ST_TIMEOUT);
                 (void)mbar_wait_bounded(&bar[0], 0u);
             }
-            cp_async_wait_all();
             return;
         }
         batch_csr_tile16(a, T, vcur, VjShared{vs}, ic_s);
@@ -225,11 +219,10 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchArgs a) {
             default: batch_csr_rows<32>(a, T, vcur, ic_s); break;
         }
     }
-    cp_async_wait_all();
     __syncthreads();
     if ((int)threadIdx.x >= T.rows) return;
     const int64_t i = T.row0 + threadIdx.x;
-    const Cell cell = staged_cell(cs, T.rows, threadIdx.x);
+    const Cell cell = load_cell(c.S, vcur, i);
     float iapp = pulse_current(c.pulses, i, t);
     if (c.iapp != nullptr) iapp += c.iapp[i];
     const CellNext o = cell_step(c.P, cell, ic_s[threadIdx.x], iapp);
@@ -557,10 +550,9 @@ static ion_status batch_plan(ion_sim *s) {
     return ION_OK;
 }
 
-// dynamic shared memory of the per-step kernel: a network's V_dend, the dense row
-// partials, then the tile's cell words (NCW x up to 256 rows)
-static size_t batch_stage_off(const BatchExt *X) { return ((size_t)X->max_dense_pad * 4 + 8 * X->R * 4 + 15) & ~(size_t)15; }
-static size_t batch_smem(const BatchExt *X) { return batch_stage_off(X) + (size_t)NCW * 256 * 4; }
+// dynamic shared memory of the per-step kernel: a network's V_dend and the dense row partials
+// (staging the tile's cell words here as well measured slower: fewer CTAs per SM)
+static size_t batch_smem(const BatchExt *X) { return (size_t)X->max_dense_pad * 4 + 8 * X->R * 4; }
 
 template <int R>
 static cudaError_t batch_launch_R(const BatchArgs &a, int tiles, size_t smem, cudaStream_t st, bool prepare) {
@@ -589,7 +581,6 @@ static cudaError_t batch_step(ion_sim *s, int k_off, const float *iapp) {
     a.col16 = s->d_col16;
     a.w = s->d_w;
     a.kahan = 1;
-    a.stage_off = (int32_t)batch_stage_off(X);
     s->launches++;
     if (X->n_tiles == 0) return cudaSuccess;
     return batch_launch(a, X->R, X->n_tiles, batch_smem(X), s->st, false);
