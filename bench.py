@@ -58,7 +58,19 @@ K3_SWEEP = (1 << 16, 1 << 18, 1 << 20, 1 << 22)
 # DRAM bytes (read + write) per launch of the line's dominant kernel, from one ncu capture
 # of that kernel in its current form (the summaries under profiles/ give the commands);
 # None where no capture matches the line's kernel and shape
-TRAFFIC = {   # (bytes per launch, source); an entry is removed when its kernel changes until re-captured
+# (bytes per launch, source, launch shape the capture used: autotuner fields that must match)
+TRAFFIC = {   # an entry is removed when its kernel changes, until it is captured again
+    ("c2", "dense_step_kernel"): (532224, "profiles/dense_step_kernel_c2_8192.md",
+                                  dict(dense_rows_per_warp=4, dense_warps=28, dense_col_splits=2)),
+    ("k3", "cell_step_kernel"): (275259392 + 241500416, "profiles/cell_step_kernel_k3_4194304.md", {}),
+    ("c3_k10", "csr_step_kernel"): (7211520, "profiles/csr_step_kernel_c3_k10.md",
+                                    dict(csr_lanes_per_row=1, csr_rows_per_cta=128)),
+    ("c3_k1000", "csr_chunk_step_kernel"): (137434880 + 2730752, "profiles/csr_chunk_step_kernel_c3_k1000.md",
+                                            dict(csr_lanes_per_row=32)),
+    ("c4", "batch_step_kernel"): (44903168 + 71936, "profiles/batch_step_kernel_c4.md", dict(dense_rows_per_warp=1)),
+    ("c5", "surrogate_tc_kernel"): (4612352, "profiles/surrogate_tc_kernel_c5.md", {}),
+    ("c2_matrix", "matrix_step_kernel"): (272269312 + 5144320, "profiles/matrix_step_kernel_c2_matrix_8192.md",
+                                          dict(dense_rows_per_warp=1)),
 }
 
 
@@ -817,9 +829,16 @@ def main():
             "clocks": ck,
         }
         tr = TRAFFIC.get((key, roof.get("kernel")))
-        if tr is not None and (key != "c3_k1000" or best == "graph"):
+        shape = dict(variants[best]["tune"] or {})
+        if args.dense_shape:
+            R, W, GJ = (int(x) for x in args.dense_shape.split(","))
+            shape.update(dense_rows_per_warp=R, dense_warps=W, dense_col_splits=GJ)
+        if key == "c2_matrix" and not shape:
+            shape["dense_rows_per_warp"] = 1          # the library's default rows per warp
+        if tr is not None and best in ("graph", "exact", "surrogate") and \
+                all(shape.get(f) == v for f, v in tr[2].items()):
             roof["traffic"] = tr[0]
-            roof["traffic_source"] = tr[1]
+            roof["traffic_source"] = tr[1] + " (one ncu capture of this kernel and launch shape)"
         # the paper's real-time criterion: one time step (50 us of biological time) computed
         # in at most 50 us of wall time
         line["real_time"] = {"us_per_timestep": roof["us_per_timestep"], "limit_us": 50.0,

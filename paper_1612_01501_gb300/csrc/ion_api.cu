@@ -810,13 +810,23 @@ static cudaError_t enqueue_one_step(ion_sim *s, int k_off, const float *iapp) {
             e = launch_sgj_dense_step(c, s->g, s->d_sgj, s->st);
             s->launches += s->lps;
         } else {
+            // the compact CSR kernels with the linear term where the network has 16-bit
+            // columns (staged or not, as for the exponential junction), else eight lanes
+            // per row over the 32-bit columns
+            const bool staged = s->csr_staged == 1 && !split;
             CsrArgs a{};
             a.c = c;
-            a.row_ptr = s->d_rowptr;
-            a.col = s->d_col;
-            a.w = s->d_w;
-            a.g = s->g;
-            e = launch_sgj_csr_step(a, s->st);
+            ion_csr_fill(s, a, staged);
+            if (a.col16 != nullptr && !split) {
+                a.lin = 1;
+                a.fuse = 1;
+                e = staged ? launch_csr_chunk_step(a, s->csr_chunk_SW, s->csr_chunk_rows, s->d_mid, s->n_chunks, false,
+                                                   s->st)
+                           : launch_csr_step(a, s->csr_SW, s->csr_rows, s->st);
+            } else {
+                a.col16 = nullptr;
+                e = launch_sgj_csr_step(a, s->st);
+            }
             s->launches++;
         }
         return e;

@@ -21,9 +21,11 @@
 namespace ion {
 
 // One CTA of 256 threads owns `rows` consecutive rows (rows <= 256).  Phase 1: groups of
-// SW lanes take the rows round-robin; phase 2: thread t updates row t.
-template <int SW, bool VEC, bool HAS_W, bool C16>
+// SW lanes take the rows round-robin; phase 2: thread t updates row t.  LIN: linear
+// junctions (the SGJ use case), on the 16-bit column layout only.
+template <int SW, bool VEC, bool HAS_W, bool C16, bool LIN = false>
 __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows) {
+    static_assert(!LIN || C16, "linear junctions run on the 16-bit column layout");
     __shared__ float ic_s[256];
     pdl_enter();
     const StepCommon &c = a.c;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
         float acc = 0.0f;
         if (e1 > e0) {   // rows past the end (and empty rows) have e0 == e1
             if (C16)
-                acc = csr_row_sum16<SW, HAS_W, false>(a.col16, a.w, e0, e1, vi, li, VjGlobal{vcur});
+                acc = csr_row_sum16<SW, HAS_W, false, LIN>(a.col16, a.w, e0, e1, vi, li, VjGlobal{vcur});
             else
                 acc = csr_row_sum<SW, VEC, HAS_W>(vcur, a.col, a.w, e0, e1, vi, li);
         }
@@ -80,13 +82,18 @@ __global__ void __launch_bounds__(256) csr_step_kernel(const CsrArgs a, int rows
     finish_cell(c, t, vnext, i, o);
 }
 
-template <int SW, bool VEC, bool HAS_W, bool C16 = false>
+template <int SW, bool VEC, bool HAS_W, bool C16 = false, bool LIN = false>
 static cudaError_t launch_csr_T(const CsrArgs &a, int rows, cudaStream_t st) {
     const int grid = (a.c.n + rows - 1) / rows;
-    return launch_k(csr_step_kernel<SW, VEC, HAS_W, C16>, dim3(grid), dim3(256), 0, st, a.c.pdl != 0, a, rows);
+    return launch_k(csr_step_kernel<SW, VEC, HAS_W, C16, LIN>, dim3(grid), dim3(256), 0, st, a.c.pdl != 0, a, rows);
 }
 template <int SW>
 static cudaError_t launch_csr_SW(const CsrArgs &a, int rows, cudaStream_t st) {
+    if (a.lin) {
+        if (a.col16 == nullptr) return cudaErrorInvalidValue;
+        return a.w != nullptr ? launch_csr_T<SW, true, true, true, true>(a, rows, st)
+                              : launch_csr_T<SW, true, false, true, true>(a, rows, st);
+    }
     if (a.col16 != nullptr)   // 16-byte aligned indices (and weights, checked at creation)
         return a.w != nullptr ? launch_csr_T<SW, true, true, true>(a, rows, st) : launch_csr_T<SW, true, false, true>(a, rows, st);
     const bool vec = ((uintptr_t)a.col % 16 == 0) && (a.w == nullptr || (uintptr_t)a.w % 16 == 0);
@@ -117,6 +124,8 @@ static void carveout_SW() {
     cudaFuncSetAttribute(csr_step_kernel<SW, false, false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     cudaFuncSetAttribute(csr_step_kernel<SW, true, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     cudaFuncSetAttribute(csr_step_kernel<SW, true, false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, true, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+    cudaFuncSetAttribute(csr_step_kernel<SW, true, false, true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
 }
 cudaError_t prepare_csr_step() {
     carveout_SW<1>();
@@ -136,9 +145,10 @@ cudaError_t prepare_csr_step() {
 // rows whose columns fall in that chunk (the per-row chunk boundaries are precomputed:
 // mid[(c-1) * n + i] is the first edge of row i in chunk c).  The gathers then hit shared
 // memory while the indices and weights stream from HBM.
-template <int SW, bool VEC, bool HAS_W, bool C16>
+template <int SW, bool VEC, bool HAS_W, bool C16, bool LIN = false>
 __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, int rows, const int32_t *mid,
                                                               int n_chunks) {
+    static_assert(!LIN || C16, "linear junctions run on the 16-bit column layout");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *vs = reinterpret_cast<float *>(smem_raw);
     float *ic_s = vs + min(CSR_CHUNK, a.c.n_pad);
@@ -225,8 +235,7 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             float acc = 0.0f;
             if (e1 > e0) {   // rows past the end (and empty segments) have e0 == e1
                 if (C16)
-                    acc = csr_row_sum16<SW, HAS_W, true>(a.col16, a.w, e0, e1, vi, li,
-                                                         VjChunk{vs});
+                    acc = csr_row_sum16<SW, HAS_W, true, LIN>(a.col16, a.w, e0, e1, vi, li, VjChunk{vs});
                 else
                     acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vi, li);
             }
@@ -254,16 +263,16 @@ size_t csr_chunk_smem_bytes(int n_pad, int rows) {
     return (size_t)(n_pad < CSR_CHUNK ? n_pad : CSR_CHUNK) * sizeof(float) + (size_t)rows * sizeof(float);
 }
 
-template <int SW, bool VEC, bool HAS_W, bool C16 = false>
+template <int SW, bool VEC, bool HAS_W, bool C16 = false, bool LIN = false>
 static cudaError_t chunk_T(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
                            cudaStream_t st) {
     const size_t smem = csr_chunk_smem_bytes(a.c.n_pad, rows);
     if (prepare)
-        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16>,
+        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (a.c.n + rows - 1) / rows;
-    return launch_k(csr_chunk_step_kernel<SW, VEC, HAS_W, C16>, dim3(grid), dim3(1024), smem, st, a.c.pdl != 0, a,
-                    rows, mid, n_chunks);
+    return launch_k(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN>, dim3(grid), dim3(1024), smem, st, a.c.pdl != 0,
+                    a, rows, mid, n_chunks);
 }
 template <int SW>
 static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
@@ -276,7 +285,14 @@ static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int 
         if (e == cudaSuccess) e = chunk_T<SW, false, false>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, true, true, true>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, true, false, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, true, true, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, false, true, true>(a, rows, mid, n_chunks, true, st);
         return e;
+    }
+    if (a.lin) {
+        if (a.col16 == nullptr) return cudaErrorInvalidValue;
+        return a.w != nullptr ? chunk_T<SW, true, true, true, true>(a, rows, mid, n_chunks, false, st)
+                              : chunk_T<SW, true, false, true, true>(a, rows, mid, n_chunks, false, st);
     }
     if (a.col16 != nullptr)
         return a.w != nullptr ? chunk_T<SW, true, true, true>(a, rows, mid, n_chunks, false, st)

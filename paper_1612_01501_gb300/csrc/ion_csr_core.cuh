@@ -11,6 +11,12 @@ __device__ __forceinline__ float gj_edge(float vi, float vj, float w) {
     const float du = (vi - vj) * GJ_SCALE;
     return w * fmaf(0.8f, ex2_approx(-du * du), 0.2f) * du;
 }
+// The junction term of one edge, in the same scaled units: LIN selects the linear
+// junction of the SGJ use case (Sec. 2.3.2), w (V_i - V_j) s, else the term above.
+template <bool LIN>
+__device__ __forceinline__ float jn_edge(float vi, float vj, float w) {
+    return LIN ? w * ((vi - vj) * GJ_SCALE) : gj_edge(vi, vj, w);
+}
 
 // Sum of one row's edges [e0, e1) handled by lane li of an SW-lane group.  VEC: the index
 // and weight arrays are 16-byte aligned, so the body of the row is read four edges per
@@ -73,10 +79,12 @@ __device__ __forceinline__ float csr_row_sum_smem(const float *vs, int c0, const
 // Two edges of row i at once through packed f32x2 arithmetic (the same terms as gj_edge):
 // dV = V_i - V_j (an FFMA2 with -1: the same bits as a subtraction), du = dV s, then
 // acc += w (0.8 2^{-du^2} + 0.2) du, the last product fused into the accumulation.
-template <bool HAS_W>
+// LIN: the linear junction, acc += w du (jn_edge).
+template <bool HAS_W, bool LIN = false>
 __device__ __forceinline__ float2 gj_edge2(float2 vi2, float2 vj2, float2 w2, float2 acc) {
     const float2 d = __ffma2_rn(vj2, make_float2(-1.0f, -1.0f), vi2);
     const float2 du = __fmul2_rn(d, make_float2(GJ_SCALE, GJ_SCALE));
+    if (LIN) return HAS_W ? __ffma2_rn(w2, du, acc) : __fadd2_rn(du, acc);
     const float2 q = __fmul2_rn(du, du);
     const float2 e = make_float2(ex2_approx(-q.x), ex2_approx(-q.y));
     float2 f = __ffma2_rn(e, make_float2(0.8f, 0.8f), make_float2(0.2f, 0.2f));
@@ -85,14 +93,14 @@ __device__ __forceinline__ float2 gj_edge2(float2 vi2, float2 vj2, float2 w2, fl
 }
 
 // Eight edges of a 16-byte group of 16-bit columns (and their weights), two at a time.
-template <bool HAS_W, class VJ>
+template <bool HAS_W, bool LIN = false, class VJ>
 __device__ __forceinline__ float csr_group16(uint4 q, float4 wa, float4 wb, float vi, VJ vj) {
     const float2 vi2 = make_float2(vi, vi);
     float2 acc = make_float2(0.0f, 0.0f);
-    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.x & 0xFFFFu), vj(q.x >> 16)), make_float2(wa.x, wa.y), acc);
-    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.y & 0xFFFFu), vj(q.y >> 16)), make_float2(wa.z, wa.w), acc);
-    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.z & 0xFFFFu), vj(q.z >> 16)), make_float2(wb.x, wb.y), acc);
-    acc = gj_edge2<HAS_W>(vi2, make_float2(vj(q.w & 0xFFFFu), vj(q.w >> 16)), make_float2(wb.z, wb.w), acc);
+    acc = gj_edge2<HAS_W, LIN>(vi2, make_float2(vj(q.x & 0xFFFFu), vj(q.x >> 16)), make_float2(wa.x, wa.y), acc);
+    acc = gj_edge2<HAS_W, LIN>(vi2, make_float2(vj(q.y & 0xFFFFu), vj(q.y >> 16)), make_float2(wa.z, wa.w), acc);
+    acc = gj_edge2<HAS_W, LIN>(vi2, make_float2(vj(q.z & 0xFFFFu), vj(q.z >> 16)), make_float2(wb.x, wb.y), acc);
+    acc = gj_edge2<HAS_W, LIN>(vi2, make_float2(vj(q.w & 0xFFFFu), vj(q.w >> 16)), make_float2(wb.z, wb.w), acc);
     return acc.x + acc.y;
 }
 template <bool HAS_W, bool LD_STREAM>
@@ -119,8 +127,9 @@ __device__ __forceinline__ uint32_t csr_ld16(const uint16_t *__restrict__ col16,
 // issues them together with its first two body groups before using any, so a row costs
 // one memory latency rather than one per part (rows of up to 16 x SW body edges are then
 // done in one round).  vj maps a 16-bit index to V_dend of that column.  LD_STREAM: the
-// indices are read once per step (evict-first), else through the read-only cache.
-template <int SW, bool HAS_W, bool LD_STREAM, class VJ>
+// indices are read once per step (evict-first), else through the read-only cache.  LIN:
+// linear junctions (jn_edge).
+template <int SW, bool HAS_W, bool LD_STREAM, bool LIN = false, class VJ>
 __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col16, const float *__restrict__ w,
                                                int e0, int e1, float vi, int li, VJ vj) {
     float acc = 0.0f;
@@ -138,13 +147,13 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
         float4 a0 = make_float4(1.0f, 1.0f, 1.0f, 1.0f), b0 = a0, a1 = a0, b1 = a0;
         if (g0) csr_load16<HAS_W, LD_STREAM>(col16, w, e, q0, a0, b0);
         if (g1) csr_load16<HAS_W, LD_STREAM>(col16, w, e + 8 * SW, q1, a1, b1);
-        if (hh) acc += gj_edge(vi, vj(jh), wh);
-        if (ht) acc += gj_edge(vi, vj(jt), wt);
-        if (g0) acc += csr_group16<HAS_W>(q0, a0, b0, vi, vj);
-        if (g1) acc += csr_group16<HAS_W>(q1, a1, b1, vi, vj);
+        if (hh) acc += jn_edge<LIN>(vi, vj(jh), wh);
+        if (ht) acc += jn_edge<LIN>(vi, vj(jt), wt);
+        if (g0) acc += csr_group16<HAS_W, LIN>(q0, a0, b0, vi, vj);
+        if (g1) acc += csr_group16<HAS_W, LIN>(q1, a1, b1, vi, vj);
         e += 16 * SW;
     } else {
-        for (int eh = e0 + li; eh < ea; eh += SW) acc += gj_edge(vi, vj(csr_ld16<LD_STREAM>(col16, eh)), HAS_W ? __ldg(w + eh) : 1.0f);
+        for (int eh = e0 + li; eh < ea; eh += SW) acc += jn_edge<LIN>(vi, vj(csr_ld16<LD_STREAM>(col16, eh)), HAS_W ? __ldg(w + eh) : 1.0f);
     }
     if (!HAS_W) {   // long rows: four groups (64 B of indices per lane) in flight per round
         for (; e + 24 * SW < eb; e += 32 * SW) {
@@ -154,8 +163,8 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
             csr_load16<false, LD_STREAM>(col16, w, e + 8 * SW, q1, u0, u1);
             csr_load16<false, LD_STREAM>(col16, w, e + 16 * SW, q2, u0, u1);
             csr_load16<false, LD_STREAM>(col16, w, e + 24 * SW, q3, u0, u1);
-            acc += (csr_group16<false>(q0, u0, u1, vi, vj) + csr_group16<false>(q1, u0, u1, vi, vj)) +
-                   (csr_group16<false>(q2, u0, u1, vi, vj) + csr_group16<false>(q3, u0, u1, vi, vj));
+            acc += (csr_group16<false, LIN>(q0, u0, u1, vi, vj) + csr_group16<false, LIN>(q1, u0, u1, vi, vj)) +
+                   (csr_group16<false, LIN>(q2, u0, u1, vi, vj) + csr_group16<false, LIN>(q3, u0, u1, vi, vj));
         }
     }
     for (; e + 8 * SW < eb; e += 16 * SW) {                 // further rounds: two groups in flight
@@ -163,16 +172,16 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
         float4 a0, b0, a1, b1;
         csr_load16<HAS_W, LD_STREAM>(col16, w, e, q0, a0, b0);
         csr_load16<HAS_W, LD_STREAM>(col16, w, e + 8 * SW, q1, a1, b1);
-        acc += csr_group16<HAS_W>(q0, a0, b0, vi, vj) + csr_group16<HAS_W>(q1, a1, b1, vi, vj);
+        acc += csr_group16<HAS_W, LIN>(q0, a0, b0, vi, vj) + csr_group16<HAS_W, LIN>(q1, a1, b1, vi, vj);
     }
     if (e < eb) {
         uint4 q;
         float4 a, b;
         csr_load16<HAS_W, LD_STREAM>(col16, w, e, q, a, b);
-        acc += csr_group16<HAS_W>(q, a, b, vi, vj);
+        acc += csr_group16<HAS_W, LIN>(q, a, b, vi, vj);
     }
     if (SW < 8)
-        for (int et = eb + li; et < e1; et += SW) acc += gj_edge(vi, vj(csr_ld16<LD_STREAM>(col16, et)), HAS_W ? __ldg(w + et) : 1.0f);
+        for (int et = eb + li; et < e1; et += SW) acc += jn_edge<LIN>(vi, vj(csr_ld16<LD_STREAM>(col16, et)), HAS_W ? __ldg(w + et) : 1.0f);
     return acc;
 }
 

@@ -261,6 +261,7 @@ struct CsrArgs {
     int32_t fuse;
     float *ic_out;
     const float *vd_in;
+    int32_t lin;          // 1: linear junctions (SGJ use case); needs col16
 };
 struct PersistArgs {
     StepCommon c;         // k_off unused: the launch runs steps *t_dev .. *t_dev + n_steps - 1

@@ -450,7 +450,7 @@ def test_csr_bank_order(torch_cuda, O, n, k):
 
 # ------------------------------------------------------------------ SGJ use case (linear junctions)
 
-def _sgj_one_step(O, n, kind, g=0.0, rp=None, col=None, w=None):
+def _sgj_one_step(O, n, kind, g=0.0, rp=None, col=None, w=None, tune=None, layout=None):
     cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 41))
     S0 = initial_state(O, cfg)
     k_or = O.DENSE_SGJ if kind == O.DENSE else O.CSR_SGJ
@@ -461,8 +461,11 @@ def _sgj_one_step(O, n, kind, g=0.0, rp=None, col=None, w=None):
     ref, _ = O.run(Sw32.astype(np.float64), 1, kind=k_or, g=g, row_ptr=rp, col=col, w=wd, t0=0,
                    iapp_dense=iapp[None, :], threads=_threads(O))
     ikind = ion.DENSE_UNIFORM if kind == O.DENSE else ion.CSR
+    kw = {} if tune is None else dict(tune=tune)
     with ion.Simulation(n, ikind, g=g, row_ptr=rp, col=col, w=w, init_state=Sw32,
-                        flags=ion.FLAG_KAHAN | ion.FLAG_SGJ) as sim:
+                        flags=ion.FLAG_KAHAN | ion.FLAG_SGJ, **kw) as sim:
+        if layout is not None:
+            layout.update(ion.ion_csr_layout(sim.h))
         sim.step(1, dense=iapp[None, :])
         got = sim.state()
     scale = g * sum_abs_dv(Sw32[0]) if kind == O.DENSE else csr_abs_scale(rp, col, w, Sw32[0])
@@ -475,15 +478,44 @@ def test_sgj_dense_one_step(torch_cuda, O, n):
     assert err.max() <= STEP_RTOL, err.max(axis=1)
 
 
-@pytest.mark.parametrize("n,k,weights", [(65536, 100, "uniform"), (1000, 7, "random")])
-def test_sgj_csr_one_step(torch_cuda, O, n, k, weights):
+# (cells, mean degree, weights, staging, expected layout): 16-bit columns for networks of
+# at most 65 536 cells with rows of 32 or more edges (the compact kernels with the linear
+# term), staged chunk by chunk when asked (40 000 cells: two chunks), 32-bit columns read
+# by eight lanes per row otherwise
+@pytest.mark.parametrize("n,k,weights,staging,index_bytes", [
+    (65536, 100, "uniform", 0, 2), (2000, 64, "random", 1, 2), (40000, 64, "uniform", 2, 2),
+    (40000, 48, "random", 2, 2), (1000, 7, "random", 0, 4)])
+def test_sgj_csr_one_step(torch_cuda, O, n, k, weights, staging, index_bytes):
     rp, col = inputs.random_symmetric_csr(n, k, 17)
     g = inputs.junction_weight(0.04, k)
     w = np.full(len(col), g, np.float32)
     if weights == "random":
         w = (w * inputs.uniform(inputs.stream_seed(n, "sgj_w"), len(col), 0.5, 1.5)).astype(np.float32)
-    err = _sgj_one_step(O, n, O.CSR, rp=rp, col=col, w=w)
+    lay = {}
+    tune = dict(csr_staging=staging) if staging else None
+    err = _sgj_one_step(O, n, O.CSR, rp=rp, col=col, w=w, tune=tune, layout=lay)
+    assert lay["index_bytes"] == index_bytes and lay["staged"] == (1 if staging == 2 else 0), lay
     assert err.max() <= STEP_RTOL, err.max(axis=1)
+
+
+def test_sgj_csr_trajectory_on_the_staged_kernel(torch_cuda, O):
+    """Linear junctions through the staged compact kernel (two chunks) for 20 ms: within
+    0.1 mV of the oracle."""
+    n, k = 40000, 40
+    rp, col = inputs.random_symmetric_csr(n, k, 23)
+    g = inputs.junction_weight(0.04, k)
+    cfg = dict(n=n, jitter=inputs.vdend_jitter(n, 43))
+    S0 = initial_state(O, cfg)
+    pulses = inputs.pulses(inputs.random_subset(n, 0.2, 43), 2.0, 12.0, 6.0)
+    with ion.Simulation(n, ion.CSR, row_ptr=rp, col=col, w=np.full(len(col), g, np.float32), init_state=S0,
+                        flags=ion.FLAG_KAHAN | ion.FLAG_SGJ, tune=dict(csr_staging=2)) as sim:
+        assert ion.ion_csr_layout(sim.h)["staged"] == 1
+        sim.set_input(pulses)
+        sim.step(400)
+        got = sim.state()
+    ref, _ = O.run(S0.astype(np.float64), 400, kind=O.CSR_SGJ, g=g, row_ptr=rp, col=col,
+                   w=np.full(len(col), g, np.float64), pulses=pulses, threads=_threads(O))
+    assert np.abs(got[:3] - ref[:3]).max() <= TRAJ_MV
 
 
 def test_sgj_c1_trajectory_100ms(torch_cuda, O):
