@@ -294,10 +294,13 @@ void ion_choose_csr_shape(double mean_deg, int *SW, int *rows) {
 }
 
 // Shared-memory staging of V_dend for a CSR network (mode 0: choose, 1: off, 2: on).
-// Staging pays when the index/weight arrays stream from HBM (they do not fit in the 129 MB
-// L2 next to the state) and rows are long enough to amortise staging every chunk per CTA:
-// measured on the 65 536-cell network, k = 1000 went from 0.45 to 0.69 of HBM bandwidth
-// while k = 100 (L2-resident) got slower.  One CTA per SM owns ceil(n / SMs) rows (at most
+// Staging pays when rows are long: a warp's 32 random gathers then cost about 3.8
+// shared-memory wavefronts instead of 32 L1 lines.  Measured: the 65 536-cell network at
+// k = 1000 went from 0.45 to 0.69 of HBM bandwidth (32-bit columns), k = 100 from 20.6 to
+// 16.9 us per step (16-bit columns), and random networks of 10 000-13 000 cells at 25-50 %
+// density ran about twice as fast staged.  The default stages rows of 64 or more edges that
+// keep 32 or more per chunk, or any CSR too large for L2 (over 96 MB) with rows of 64 or
+// more edges; rows of ~10 edges stay on the direct kernel.  One CTA per SM owns ceil(n / SMs) rows (at most
 // 1024).  Only
 // CSR arrays copied from the host are staged: their columns were checked to be sorted
 // and in range, which the chunk boundaries rely on.
@@ -321,10 +324,12 @@ void ion_csr_fill(const ion_sim *s, CsrArgs &a, bool staged) {
 ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
     const double deg = s->n > 0 ? (double)s->nnz / s->n : 0.0;
     const double csr_bytes = (double)((s->d_col16 ? 2 : 4) + (s->d_w ? 4 : 0)) * (double)s->nnz;
-    const bool on = mode == 2 || (mode == 0 && deg >= 64.0 && csr_bytes > 96.0e6);
+    const double chunks = (double)((s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK);
+    const bool on = mode == 2 || (mode == 0 && deg >= 64.0 && (csr_bytes > 96.0e6 || deg / chunks >= 32.0));
     s->csr_staged = 0;
     // staging relies on validated (sorted, in-range) columns: host-copied CSR only
-    if (!on || (s->flags & ION_FLAG_SPLIT) || !s->own_csr || s->d_rev) return ION_OK;
+    // (the surrogate path computes its gap currents with the direct kernel)
+    if (!on || (s->flags & (ION_FLAG_SPLIT | ION_FLAG_SURROGATE)) || !s->own_csr || s->d_rev) return ION_OK;
     s->n_chunks = (s->n_pad + CSR_CHUNK - 1) / CSR_CHUNK;
     int rows = (s->n + s->sms - 1) / s->sms;
     if (rows > 1024) rows = 1024;

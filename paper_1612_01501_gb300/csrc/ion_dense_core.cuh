@@ -101,12 +101,17 @@ __device__ __forceinline__ bool gj_pass(const DenseSmem &sm, const float *src, i
         const float4 *t4 = reinterpret_cast<const float4 *>(tb);
         const int real = max(0, min(len, n - j0));   // real columns of this tile
         const int n4 = (real + 3) >> 2;               // float4 columns that hold any
-        for (int m0 = cs * 32 + lane; m0 < n4; m0 += 32 * GJ * BLK) {
+        // The pair loop runs to a multiple of 32 float4 columns (within the padded tile),
+        // so that a warp's 32 lanes are all in range or all out: no lane of a warp takes
+        // the checked path while another takes the unchecked one.  The columns added are
+        // sentinel padding, whose pairs contribute exactly 0.
+        const int n4w = min((n4 + 31) & ~31, len >> 2);
+        for (int m0 = cs * 32 + lane; m0 < n4w; m0 += 32 * GJ * BLK) {
             float2 acc[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) acc[r] = make_float2(0.0f, 0.0f);
-            if (m0 + (BLK - 1) * 32 * GJ < n4) gj_block<R, GJ, BLK, false>(t4, m0, n4, negm2, negs2, u2, acc);
-            else gj_block<R, GJ, BLK, true>(t4, m0, n4, negm2, negs2, u2, acc);
+            if (m0 + (BLK - 1) * 32 * GJ < n4w) gj_block<R, GJ, BLK, false>(t4, m0, n4w, negm2, negs2, u2, acc);
+            else gj_block<R, GJ, BLK, true>(t4, m0, n4w, negm2, negs2, u2, acc);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const float blk = acc[r].x + acc[r].y;

@@ -478,14 +478,15 @@ def test_sgj_dense_one_step(torch_cuda, O, n):
     assert err.max() <= STEP_RTOL, err.max(axis=1)
 
 
-# (cells, mean degree, weights, staging, expected layout): 16-bit columns for networks of
-# at most 65 536 cells with rows of 32 or more edges (the compact kernels with the linear
-# term), staged chunk by chunk when asked (40 000 cells: two chunks), 32-bit columns read
-# by eight lanes per row otherwise
-@pytest.mark.parametrize("n,k,weights,staging,index_bytes", [
-    (65536, 100, "uniform", 0, 2), (2000, 64, "random", 1, 2), (40000, 64, "uniform", 2, 2),
-    (40000, 48, "random", 2, 2), (1000, 7, "random", 0, 4)])
-def test_sgj_csr_one_step(torch_cuda, O, n, k, weights, staging, index_bytes):
+# (cells, mean degree, weights, staging asked (0: the default), expected layout): 16-bit
+# columns for networks of at most 65 536 cells with rows of 32 or more edges (the compact
+# kernels with the linear term), staged chunk by chunk when asked or when rows are long
+# (the default stages rows of 64 or more edges that keep 32 or more per 32 768-cell chunk),
+# 32-bit columns read by eight lanes per row otherwise
+@pytest.mark.parametrize("n,k,weights,staging,index_bytes,staged", [
+    (65536, 100, "uniform", 0, 2, 1), (2000, 64, "random", 1, 2, 0), (40000, 64, "uniform", 2, 2, 1),
+    (40000, 48, "random", 2, 2, 1), (1000, 7, "random", 0, 4, 0)])
+def test_sgj_csr_one_step(torch_cuda, O, n, k, weights, staging, index_bytes, staged):
     rp, col = inputs.random_symmetric_csr(n, k, 17)
     g = inputs.junction_weight(0.04, k)
     w = np.full(len(col), g, np.float32)
@@ -494,7 +495,7 @@ def test_sgj_csr_one_step(torch_cuda, O, n, k, weights, staging, index_bytes):
     lay = {}
     tune = dict(csr_staging=staging) if staging else None
     err = _sgj_one_step(O, n, O.CSR, rp=rp, col=col, w=w, tune=tune, layout=lay)
-    assert lay["index_bytes"] == index_bytes and lay["staged"] == (1 if staging == 2 else 0), lay
+    assert lay["index_bytes"] == index_bytes and lay["staged"] == staged, lay
     assert err.max() <= STEP_RTOL, err.max(axis=1)
 
 
