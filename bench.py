@@ -65,8 +65,6 @@ TRAFFIC = {   # an entry is removed when its kernel changes, until it is capture
     ("k3", "cell_step_kernel"): (275259392 + 241500416, "profiles/cell_step_kernel_k3_4194304.md", {}),
     ("c3_k10", "csr_step_kernel"): (7211520, "profiles/csr_step_kernel_c3_k10.md",
                                     dict(csr_lanes_per_row=1, csr_rows_per_cta=128)),
-    ("c3_k1000", "csr_chunk_step_kernel"): (137434880 + 2730752, "profiles/csr_chunk_step_kernel_c3_k1000.md",
-                                            dict(csr_lanes_per_row=32)),
     ("c4", "batch_step_kernel"): (44903168 + 71936, "profiles/batch_step_kernel_c4.md", dict(dense_rows_per_warp=1)),
     ("c5", "surrogate_tc_kernel"): (4612352, "profiles/surrogate_tc_kernel_c5.md", {}),
     ("c2_matrix", "matrix_step_kernel"): (272269312 + 5144320, "profiles/matrix_step_kernel_c2_matrix_8192.md",

@@ -319,6 +319,55 @@ void ion_csr_fill(const ion_sim *s, CsrArgs &a, bool staged) {
     a.w = s->d_w;
     a.g = s->g;
     a.col16 = csr_use16(s, staged) ? s->d_col16 : nullptr;
+    if (staged && s->d_col16p && a.col16 && s->pad_rows == s->csr_chunk_rows) {
+        a.col16p = s->d_col16p;
+        a.wp = s->d_wp;
+        a.segoff = s->d_segoff;
+    }
+}
+
+// The staged kernel's padded layout (see ion_sim): segment offsets on the host from the row
+// pointers and chunk boundaries, the columns and weights by a fill kernel.
+static ion_status build_padded_layout(ion_sim *s) {
+    const int n = s->n, C = s->n_chunks, rows = s->csr_chunk_rows;
+    std::vector<int32_t> rp((size_t)n + 1), mid((size_t)(C - 1) * n);
+    cudaError_t e = cudaMemcpyAsync(rp.data(), s->d_rowptr, rp.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess && C > 1)
+        e = cudaMemcpyAsync(mid.data(), s->d_mid, mid.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return ion_fail(nullptr, ION_ERR_CUDA, "CSR padded layout: %s", cudaGetErrorString(e));
+    std::vector<int32_t> off((size_t)C * n + 1);
+    int64_t tot = 0;
+    for (int ch = 0; ch < C; ++ch)
+        for (int i = 0; i < n; ++i) {
+            const int64_t b = ch == 0 ? rp[i] : mid[(size_t)(ch - 1) * n + i];
+            const int64_t en = ch == C - 1 ? rp[i + 1] : mid[(size_t)ch * n + i];
+            off[(size_t)ch * n + i] = (int32_t)tot;
+            tot += (en - b + 7) & ~(int64_t)7;
+            if (tot >= INT32_MAX) return ION_OK;   // too large for 32-bit offsets: keep the unpadded layout
+        }
+    off[(size_t)C * n] = (int32_t)tot;
+    e = ion_alloc(&s->d_segoff, off.size() * sizeof(int32_t));
+    if (e == cudaSuccess) e = ion_alloc(&s->d_col16p, (size_t)std::max<int64_t>(tot, 8) * sizeof(uint16_t));
+    if (e == cudaSuccess && s->d_w) e = ion_alloc(&s->d_wp, (size_t)std::max<int64_t>(tot, 8) * sizeof(float));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->d_segoff, off.data(), off.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess)
+        e = launch_csr_pad_fill(s->d_rowptr, s->d_mid, s->d_col, s->d_w, n, C, rows, std::min(CSR_CHUNK, s->n_pad),
+                                s->d_segoff, s->d_col16p, s->d_wp, s->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);   // the host offsets are released on return
+    if (e != cudaSuccess) {
+        cudaFree(s->d_segoff);
+        cudaFree(s->d_col16p);
+        cudaFree(s->d_wp);
+        s->d_segoff = nullptr;
+        s->d_col16p = nullptr;
+        s->d_wp = nullptr;
+        return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "CSR padded layout: %s",
+                        cudaGetErrorString(e));
+    }
+    s->pad_rows = rows;
+    return ION_OK;
 }
 
 ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
@@ -344,6 +393,10 @@ ion_status ion_setup_csr_staging(ion_sim *s, int mode) {
         if (e != cudaSuccess)
             return ion_fail(nullptr, e == cudaErrorMemoryAllocation ? ION_ERR_OOM : ION_ERR_CUDA, "CSR staging setup: %s",
                             cudaGetErrorString(e));
+    }
+    if (s->d_col16 && !s->col16_bank && !s->d_col16p) {
+        const ion_status sp = build_padded_layout(s);
+        if (sp != ION_OK) return sp;
     }
     const ion_status st = ion_prepare_csr_chunk(s);
     if (st != ION_OK) return st;
@@ -436,6 +489,9 @@ void ion_sim_free_device(ion_sim *s) {
     s->d_split = s->d_rev = nullptr;
     s->d_slot = s->d_icu = nullptr;
     cudaFree(s->d_mid);
+    cudaFree(s->d_col16p);
+    cudaFree(s->d_wp);
+    cudaFree(s->d_segoff);
     cudaFree(s->d_mlp);
     cudaFree(s->d_mlp_tc);
     s->d_mlp_tc = nullptr;
@@ -622,9 +678,10 @@ extern "C" ion_status ion_create(const ion_net *net, const ion_conn *conn, const
                 const ion_tune *tb = (const ion_tune *)params->tune;
                 std::vector<uint16_t> h16;   // opt-in: bank order (uniform weights only: no weight array to permute)
                 if (tb && tb->csr_bank_order == 1 && !keep_w &&
-                    ion_csr_bank_col16(s->n, s->n_pad, conn->row_ptr, conn->col_idx, h16))
+                    ion_csr_bank_col16(s->n, s->n_pad, conn->row_ptr, conn->col_idx, h16)) {
                     e = cudaMemcpy(s->d_col16, h16.data(), h16.size() * sizeof(uint16_t), cudaMemcpyHostToDevice);
-                else
+                    s->col16_bank = true;
+                } else
                     e = launch_csr_col16(s->d_col, s->nnz, round_up(s->nnz, 8), s->d_col16, s->st);
             }
             if (e != cudaSuccess) return fail(ion_fail(nullptr, ION_ERR_CUDA, "ion_create: CSR copy: %s", cudaGetErrorString(e)));

@@ -145,13 +145,18 @@ cudaError_t prepare_csr_step() {
 // rows whose columns fall in that chunk (the per-row chunk boundaries are precomputed:
 // mid[(c-1) * n + i] is the first edge of row i in chunk c).  The gathers then hit shared
 // memory while the indices and weights stream from HBM.
-template <int SW, bool VEC, bool HAS_W, bool C16, bool LIN = false>
+// PAD: the padded layout (a.col16p, a.wp, a.segoff): every (chunk, row) segment is whole
+// 16-byte groups of chunk-relative columns, its padding entries index vs[nb + row offset],
+// which holds the row's own V_dend (a term with dV = 0, exactly 0); no head or tail edges.
+template <int SW, bool VEC, bool HAS_W, bool C16, bool LIN = false, bool PAD = false>
 __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, int rows, const int32_t *mid,
                                                               int n_chunks) {
     static_assert(!LIN || C16, "linear junctions run on the 16-bit column layout");
+    static_assert(!PAD || C16, "the padded layout has 16-bit columns");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *vs = reinterpret_cast<float *>(smem_raw);
-    float *ic_s = vs + min(CSR_CHUNK, a.c.n_pad);
+    const int nb = min(CSR_CHUNK, a.c.n_pad);
+    float *ic_s = vs + nb + rows;   // vs[nb .. nb + rows): the rows' own V_dend (PAD)
     __shared__ __align__(8) uint64_t bar;
     pdl_enter();
     const StepCommon &c = a.c;
@@ -166,7 +171,10 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
         mbar_init(&bar, 1);
         fence_mbar_init();
     }
-    for (int r = threadIdx.x; r < rows; r += blockDim.x) ic_s[r] = 0.0f;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+        ic_s[r] = 0.0f;
+        if (PAD) vs[nb + r] = row0 + r < n ? vcur[row0 + r] : 0.0f;   // past the chunk: never overwritten
+    }
     __syncthreads();
     for (int ch = 0; ch < n_chunks; ++ch) {
         const int c0 = ch * CSR_CHUNK;
@@ -192,8 +200,13 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             e0 = e1 = 0;
             vi = 0.0f;
             if (it < iters && rr < rows && i < n) {
-                e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
-                e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+                if (PAD) {   // chunk-major segments: (ch, i + 1) starts where (ch, i) ends
+                    e0 = a.segoff[(int64_t)ch * n + i];
+                    e1 = a.segoff[(int64_t)ch * n + i + 1];
+                } else {
+                    e0 = ch == 0 ? a.row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
+                    e1 = ch == n_chunks - 1 ? a.row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+                }
                 vi = vcur[i];
             }
         };
@@ -217,16 +230,18 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
                 vin = vim;
                 bounds(it + 2, e0m, e1m, vim);
                 if (li == 0 && e1n > e0n) {   // the next row's stream, in whole 16-byte groups
-                    if (C16) {   // col16 is padded to whole 16-byte groups
+                    if (C16) {   // col16 (and col16p) are padded to whole 16-byte groups
                         const int64_t b0 = ((int64_t)e0n * 2) & ~(int64_t)15, b1 = ((int64_t)e1n * 2 + 15) & ~(int64_t)15;
-                        bulk_prefetch_l2(reinterpret_cast<const char *>(a.col16) + b0, (uint32_t)(b1 - b0));
+                        bulk_prefetch_l2(reinterpret_cast<const char *>(PAD ? a.col16p : a.col16) + b0,
+                                         (uint32_t)(b1 - b0));
                     } else {     // 32-bit columns: the last partial group is left out
                         const int64_t b0 = ((int64_t)e0n * 4) & ~(int64_t)15, b1 = ((int64_t)e1n * 4) & ~(int64_t)15;
                         if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const char *>(a.col) + b0, (uint32_t)(b1 - b0));
                     }
                     if (HAS_W) {
                         const int64_t b0 = ((int64_t)e0n * 4) & ~(int64_t)15, b1 = ((int64_t)e1n * 4) & ~(int64_t)15;
-                        if (b1 > b0) bulk_prefetch_l2(reinterpret_cast<const char *>(a.w) + b0, (uint32_t)(b1 - b0));
+                        if (b1 > b0)
+                            bulk_prefetch_l2(reinterpret_cast<const char *>(PAD ? a.wp : a.w) + b0, (uint32_t)(b1 - b0));
                     }
                 }
             } else {
@@ -234,7 +249,9 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
             }
             float acc = 0.0f;
             if (e1 > e0) {   // rows past the end (and empty segments) have e0 == e1
-                if (C16)
+                if (PAD)
+                    acc = csr_row_sum16<SW, HAS_W, true, LIN, true>(a.col16p, a.wp, e0, e1, vi, li, VjPadded{vs});
+                else if (C16)
                     acc = csr_row_sum16<SW, HAS_W, true, LIN>(a.col16, a.w, e0, e1, vi, li, VjChunk{vs});
                 else
                     acc = csr_row_sum_smem<SW, VEC, HAS_W>(vs, c0, a.col, a.w, e0, e1, vi, li);
@@ -259,20 +276,21 @@ __global__ void __launch_bounds__(1024) csr_chunk_step_kernel(const CsrArgs a, i
     }
 }
 
+// the chunk, the rows' own V_dend (padded layout) and their currents
 size_t csr_chunk_smem_bytes(int n_pad, int rows) {
-    return (size_t)(n_pad < CSR_CHUNK ? n_pad : CSR_CHUNK) * sizeof(float) + (size_t)rows * sizeof(float);
+    return (size_t)(n_pad < CSR_CHUNK ? n_pad : CSR_CHUNK) * sizeof(float) + 2 * (size_t)rows * sizeof(float);
 }
 
-template <int SW, bool VEC, bool HAS_W, bool C16 = false, bool LIN = false>
+template <int SW, bool VEC, bool HAS_W, bool C16 = false, bool LIN = false, bool PAD = false>
 static cudaError_t chunk_T(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
                            cudaStream_t st) {
     const size_t smem = csr_chunk_smem_bytes(a.c.n_pad, rows);
     if (prepare)
-        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN>,
+        return cudaFuncSetAttribute(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN, PAD>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int grid = (a.c.n + rows - 1) / rows;
-    return launch_k(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN>, dim3(grid), dim3(1024), smem, st, a.c.pdl != 0,
-                    a, rows, mid, n_chunks);
+    return launch_k(csr_chunk_step_kernel<SW, VEC, HAS_W, C16, LIN, PAD>, dim3(grid), dim3(1024), smem, st,
+                    a.c.pdl != 0, a, rows, mid, n_chunks);
 }
 template <int SW>
 static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int n_chunks, bool prepare,
@@ -287,7 +305,18 @@ static cudaError_t chunk_SW(const CsrArgs &a, int rows, const int32_t *mid, int 
         if (e == cudaSuccess) e = chunk_T<SW, true, false, true>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, true, true, true, true>(a, rows, mid, n_chunks, true, st);
         if (e == cudaSuccess) e = chunk_T<SW, true, false, true, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, true, true, false, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, false, true, false, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, true, true, true, true>(a, rows, mid, n_chunks, true, st);
+        if (e == cudaSuccess) e = chunk_T<SW, true, false, true, true, true>(a, rows, mid, n_chunks, true, st);
         return e;
+    }
+    if (a.col16p != nullptr) {   // the padded layout (weights in a.wp when per edge)
+        if (a.lin)
+            return a.wp != nullptr ? chunk_T<SW, true, true, true, true, true>(a, rows, mid, n_chunks, false, st)
+                                   : chunk_T<SW, true, false, true, true, true>(a, rows, mid, n_chunks, false, st);
+        return a.wp != nullptr ? chunk_T<SW, true, true, true, false, true>(a, rows, mid, n_chunks, false, st)
+                               : chunk_T<SW, true, false, true, false, true>(a, rows, mid, n_chunks, false, st);
     }
     if (a.lin) {
         if (a.col16 == nullptr) return cudaErrorInvalidValue;
@@ -334,6 +363,35 @@ __global__ void csr_chunk_bounds_kernel(const int32_t *row_ptr, const int32_t *c
         }
         mid[(int64_t)(ch - 1) * n + i] = lo;
     }
+}
+
+// The padded layout from the sorted CSR: one warp per (chunk, row) segment, in chunk-major
+// order at off[seg]; columns chunk-relative, then padding entries nb + (i mod rows) (the
+// slot of row i's own V_dend in its CTA) up to the next multiple of 8, weight 0.
+__global__ void csr_pad_fill_kernel(const int32_t *row_ptr, const int32_t *mid, const int32_t *col, const float *w,
+                                    int32_t n, int n_chunks, int rows, int nb, const int32_t *off, uint16_t *col16p,
+                                    float *wp) {
+    const int64_t seg = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (seg >= (int64_t)n_chunks * n) return;
+    const int ch = (int)(seg / n), i = (int)(seg % n);
+    const int b = ch == 0 ? row_ptr[i] : mid[(int64_t)(ch - 1) * n + i];
+    const int e = ch == n_chunks - 1 ? row_ptr[i + 1] : mid[(int64_t)ch * n + i];
+    const int o = off[seg], len = off[seg + 1] - o;
+    for (int k = lane; k < len; k += 32) {
+        const bool real = k < e - b;
+        col16p[o + k] = (uint16_t)(real ? col[b + k] - ch * CSR_CHUNK : nb + i % rows);
+        if (wp) wp[o + k] = real ? w[b + k] : 0.0f;
+    }
+}
+
+cudaError_t launch_csr_pad_fill(const int32_t *row_ptr, const int32_t *mid, const int32_t *col, const float *w,
+                                int32_t n, int n_chunks, int rows, int nb, const int32_t *off, uint16_t *col16p,
+                                float *wp, cudaStream_t st) {
+    const int64_t segs = (int64_t)n_chunks * n;
+    csr_pad_fill_kernel<<<(unsigned)((segs + 7) / 8), 256, 0, st>>>(row_ptr, mid, col, w, n, n_chunks, rows, nb, off,
+                                                                     col16p, wp);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks, int32_t *mid,

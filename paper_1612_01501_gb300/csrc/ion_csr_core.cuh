@@ -128,17 +128,18 @@ __device__ __forceinline__ uint32_t csr_ld16(const uint16_t *__restrict__ col16,
 // one memory latency rather than one per part (rows of up to 16 x SW body edges are then
 // done in one round).  vj maps a 16-bit index to V_dend of that column.  LD_STREAM: the
 // indices are read once per step (evict-first), else through the read-only cache.  LIN:
-// linear junctions (jn_edge).
-template <int SW, bool HAS_W, bool LD_STREAM, bool LIN = false, class VJ>
+// linear junctions (jn_edge).  ALIGNED: e0 and e1 are multiples of 8 (the padded layout),
+// so the row is all body.
+template <int SW, bool HAS_W, bool LD_STREAM, bool LIN = false, bool ALIGNED = false, class VJ>
 __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col16, const float *__restrict__ w,
                                                int e0, int e1, float vi, int li, VJ vj) {
     float acc = 0.0f;
-    const int ea = min(e1, (e0 + 7) & ~7);                 // first 16-byte aligned edge
-    const int eb = ea + ((e1 - ea) & ~7);                   // end of the aligned body
+    const int ea = ALIGNED ? e0 : min(e1, (e0 + 7) & ~7);   // first 16-byte aligned edge
+    const int eb = ALIGNED ? e1 : ea + ((e1 - ea) & ~7);     // end of the aligned body
     int e = ea + 8 * li;
     if (SW >= 8) {
         const int eh = e0 + li, et = eb + li;
-        const bool hh = eh < ea, ht = et < e1;
+        const bool hh = !ALIGNED && eh < ea, ht = !ALIGNED && et < e1;
         const uint32_t jh = hh ? csr_ld16<LD_STREAM>(col16, eh) : 0u;
         const uint32_t jt = ht ? csr_ld16<LD_STREAM>(col16, et) : 0u;
         const float wh = (HAS_W && hh) ? __ldg(w + eh) : 1.0f, wt = (HAS_W && ht) ? __ldg(w + et) : 1.0f;
@@ -152,7 +153,7 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
         if (g0) acc += csr_group16<HAS_W, LIN>(q0, a0, b0, vi, vj);
         if (g1) acc += csr_group16<HAS_W, LIN>(q1, a1, b1, vi, vj);
         e += 16 * SW;
-    } else {
+    } else if (!ALIGNED) {
         for (int eh = e0 + li; eh < ea; eh += SW) acc += jn_edge<LIN>(vi, vj(csr_ld16<LD_STREAM>(col16, eh)), HAS_W ? __ldg(w + eh) : 1.0f);
     }
     if (!HAS_W) {   // long rows: four groups (64 B of indices per lane) in flight per round
@@ -180,7 +181,7 @@ __device__ __forceinline__ float csr_row_sum16(const uint16_t *__restrict__ col1
         csr_load16<HAS_W, LD_STREAM>(col16, w, e, q, a, b);
         acc += csr_group16<HAS_W, LIN>(q, a, b, vi, vj);
     }
-    if (SW < 8)
+    if (SW < 8 && !ALIGNED)
         for (int et = eb + li; et < e1; et += SW) acc += jn_edge<LIN>(vi, vj(csr_ld16<LD_STREAM>(col16, et)), HAS_W ? __ldg(w + et) : 1.0f);
     return acc;
 }
@@ -203,6 +204,12 @@ static_assert(CSR_CHUNK == 32768, "chunk-relative columns are the low 15 bits");
 struct VjChunk {
     const float *vs;
     __device__ __forceinline__ float operator()(uint32_t j) const { return vs[j & 0x7FFFu]; }
+};
+// The padded layout's columns are chunk-relative already; the padding entries index slots
+// past the chunk that hold each row's own V_dend
+struct VjPadded {
+    const float *vs;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return vs[j]; }
 };
 
 }  // namespace ion

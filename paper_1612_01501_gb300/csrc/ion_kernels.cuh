@@ -262,6 +262,10 @@ struct CsrArgs {
     float *ic_out;
     const float *vd_in;
     int32_t lin;          // 1: linear junctions (SGJ use case); needs col16
+    // staged kernel, padded layout (see ion_sim): columns, weights, segment offsets
+    const uint16_t *col16p;
+    const float *wp;
+    const int32_t *segoff;
 };
 struct PersistArgs {
     StepCommon c;         // k_off unused: the launch runs steps *t_dev .. *t_dev + n_steps - 1
@@ -317,6 +321,9 @@ cudaError_t launch_sgj_csr_step(const CsrArgs &a, cudaStream_t st);
 cudaError_t launch_csr_col16(const int32_t *col, int64_t nnz, int64_t n_alloc, uint16_t *col16, cudaStream_t st);
 cudaError_t launch_csr_half_step(const CsrArgs &a, int lanes_per_row, int rows_per_cta, const int32_t *split,
                                  const int32_t *rev, float *slot, float *icu, cudaStream_t st);
+cudaError_t launch_csr_pad_fill(const int32_t *row_ptr, const int32_t *mid, const int32_t *col, const float *w,
+                                 int32_t n, int n_chunks, int rows, int nb, const int32_t *off, uint16_t *col16p,
+                                 float *wp, cudaStream_t st);
 cudaError_t launch_csr_chunk_bounds(const int32_t *row_ptr, const int32_t *col, int32_t n, int n_chunks,
                                     int32_t *mid, cudaStream_t st);
 size_t csr_chunk_smem_bytes(int n_pad, int rows);

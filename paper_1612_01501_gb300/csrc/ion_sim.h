@@ -71,6 +71,14 @@ struct ion_sim {
     int csr_staged = 0;             // 1: V_dend staged in shared memory chunk by chunk
     int csr_chunk_SW = 32, csr_chunk_rows = 0, n_chunks = 1;
     int32_t *d_mid = nullptr;       // interior chunk boundaries per row
+    // the staged kernel's padded layout: each (chunk, row) segment's columns chunk-relative
+    // and padded to whole 16-byte groups with entries that index the row's own V_dend
+    // (a pair with dV = 0 adds exactly 0); segments in chunk-major order from d_segoff
+    uint16_t *d_col16p = nullptr;
+    float *d_wp = nullptr;
+    int32_t *d_segoff = nullptr;
+    int32_t pad_rows = 0;           // rows per CTA the padding entries are numbered for
+    bool col16_bank = false;        // col16 holds the opt-in bank order (no padded layout)
     // half-work CSR (ION_FLAG_HALF_WORK on a CSR network): first upper edge of each row, the
     // mirrored position of every upper edge, the per-edge slots, the rows' upper sums
     int32_t *d_split = nullptr, *d_rev = nullptr;
