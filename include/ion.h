@@ -210,7 +210,9 @@ typedef struct {
     int32_t csr_rows_per_cta;    /* rows per CTA of 256 threads, 1..256             */
     int32_t csr_lanes_scale;     /* batches: 0 = lanes per row from each network's
                                     mean degree, +1 = twice that, -1 = half        */
-    int32_t csr_staging;         /* single CSR networks: 0 = choose, 1 = gather V_dend
+    int32_t csr_staging;         /* single CSR networks: 0 = choose (stage when the
+                                    mean degree is 64 or more and at least 32 per
+                                    chunk, or the CSR exceeds 96 MB), 1 = gather V_dend
                                     through L1/L2, 2 = stage V_dend in shared memory
                                     128 KB at a time (one CTA per SM)                */
     int32_t csr_bank_order;      /* single CSR networks with equal weights: 1 = store the
@@ -317,7 +319,10 @@ ion_status ion_autotune(ion_sim *sim, int32_t steps, ion_tune *chosen);
  *                 its chunk fits in 16 bits), or the network has at most 65 536 cells and a
  *                 mean degree of at least 32; else 4;
  *   *weight_bytes 0 when every weight is bitwise equal (one scalar is kept), else 4;
- *   *staged       1 when V_dend is staged in shared memory chunk by chunk, else 0.
+ *   *staged       1 when V_dend is staged in shared memory chunk by chunk, else 0.  A
+ *                 staged handle also keeps its columns chunk by chunk, each row's segment
+ *                 padded to a multiple of 8 with entries that pair the row with itself
+ *                 (dV = 0: they add exactly 0); the figures above count the stored edges.
  * Both compactions are exact: the kernels evaluate the same edges with the same values.
  * ION_FLAG_CSR_AS_GIVEN turns them off.  Dense / NGJ handles report 0, 0, 0.  Any output
  * pointer may be NULL. */
