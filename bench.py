@@ -65,10 +65,18 @@ TRAFFIC = {   # an entry is removed when its kernel changes, until it is capture
     ("k3", "cell_step_kernel"): (275259392 + 241500416, "profiles/cell_step_kernel_k3_4194304.md", {}),
     ("c3_k10", "csr_step_kernel"): (7211520, "profiles/csr_step_kernel_c3_k10.md",
                                     dict(csr_lanes_per_row=1, csr_rows_per_cta=128)),
-    ("c4", "batch_step_kernel"): (44903168 + 71936, "profiles/batch_step_kernel_c4.md", dict(dense_rows_per_warp=1)),
+    # captured at 32 lanes per row: the DRAM bytes are those of the padded layout (each
+    # index byte and state word read once), the same for any lane count
+    ("c3_k1000", "csr_chunk_step_kernel"): (135862784 + 2681600, "profiles/csr_chunk_step_kernel_c3_k1000.md",
+                                            dict(csr_staging=2)),
+    # captured with 8-row dense tiles: the DRAM bytes (state, CSR indices; V_dend tiles
+    # come from L2) are read once per step whatever the tile shape
+    ("c3_k100", "csr_chunk_step_kernel"): (18866432, "profiles/csr_chunk_step_kernel_c3_k100.md", dict(csr_staging=2)),
+    ("c2_sgj", "sgj_dense_update_kernel"): (517376, "profiles/sgj_dense_update_kernel_c2_sgj_8192.md", {}),
+    ("c4", "batch_step_kernel"): (44903168 + 71936, "profiles/batch_step_kernel_c4.md", {}),
     ("c5", "surrogate_tc_kernel"): (4612352, "profiles/surrogate_tc_kernel_c5.md", {}),
-    ("c2_matrix", "matrix_step_kernel"): (272269312 + 5144320, "profiles/matrix_step_kernel_c2_matrix_8192.md",
-                                          dict(dense_rows_per_warp=1)),
+    # captured at one row per warp: every weight is streamed once whatever the rows per warp
+    ("c2_matrix", "matrix_step_kernel"): (272269312 + 5144320, "profiles/matrix_step_kernel_c2_matrix_8192.md", {}),
 }
 
 
@@ -831,8 +839,6 @@ def main():
         if args.dense_shape:
             R, W, GJ = (int(x) for x in args.dense_shape.split(","))
             shape.update(dense_rows_per_warp=R, dense_warps=W, dense_col_splits=GJ)
-        if key == "c2_matrix" and not shape:
-            shape["dense_rows_per_warp"] = 1          # the library's default rows per warp
         if tr is not None and best in ("graph", "exact", "surrogate") and \
                 all(shape.get(f) == v for f, v in tr[2].items()):
             roof["traffic"] = tr[0]
