@@ -842,7 +842,7 @@ def main():
         if tr is not None and best in ("graph", "exact", "surrogate") and \
                 all(shape.get(f) == v for f, v in tr[2].items()):
             roof["traffic"] = tr[0]
-            roof["traffic_source"] = tr[1] + " (one ncu capture of this kernel and launch shape)"
+            roof["traffic_source"] = tr[1] + " (one ncu capture of this kernel; the summary names its launch shape)"
         # the paper's real-time criterion: one time step (50 us of biological time) computed
         # in at most 50 us of wall time
         line["real_time"] = {"us_per_timestep": roof["us_per_timestep"], "limit_us": 50.0,
