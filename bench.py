@@ -291,22 +291,59 @@ def rt_graph(torch, n: int, density: float, seed: int, device: str = "cuda"):
     return row_ptr.to(torch.int32).cpu().numpy(), torch.cat(cols).cpu().numpy()
 
 
+def rt_search(time_at, n0, p, limit=RT_LIMIT_US, quantum=64):
+    """The largest size N (a multiple of `quantum`) with time_at(N) <= limit, for a step time
+    that grows with N.  Measure n0; then up to four model steps: fit t(N) = 3 + a N^p to the
+    last measurement and measure the size predicted for 0.98 x limit; then bisect the
+    bracket [largest size within the limit, smallest size over it] until it is within 2 %
+    or one quantum (halving or growing by 10 % while one side is missing).  Returns
+    (largest size within the limit or None, {size: time} of every measurement)."""
+    tried = {}
+
+    def measure(N):
+        N = max(quantum, int(round(N / float(quantum))) * quantum)
+        if N not in tried:
+            tried[N] = time_at(N)
+        return N, tried[N]
+
+    def sides():
+        return [k for k, v in tried.items() if v <= limit], [k for k, v in tried.items() if v > limit]
+
+    N, t = measure(n0)
+    for _ in range(4):   # model steps
+        a = max(t - 3.0, 0.05) / float(N) ** p
+        N, t = measure(((0.98 * limit - 3.0) / a) ** (1.0 / p))
+        ok, bad = sides()
+        if ok and bad and min(bad) <= 1.02 * max(ok):
+            break
+    for _ in range(6):   # bisection
+        ok, bad = sides()
+        if not ok:
+            measure(min(tried) // 2)
+            continue
+        if not bad:
+            measure(max(ok) * 1.1)
+            continue
+        lo, hi = max(ok), min(bad)
+        if hi <= 1.02 * lo or hi - lo <= quantum:
+            break
+        measure((lo + hi) / 2)
+    ok, _ = sides()
+    return (max(ok) if ok else None), tried
+
+
 def rt_table(ion, torch, stream, warmup):
     """Largest network whose time step is computed within 50 us, per use case of the
     paper's real-time table, on one GPU, steps back to back (CUDA-graph replay).  Each
-    size is measured over 2000 steps after `warmup` x 200 untimed ones; the search fits
-    t(N) = 3 us + a N^p to the last measurement, measures the predicted size, and closes
-    the bracket by bisection to 2 %.  Also: per-step latency with the host in the loop at
-    that size (each step's evoked input written from host memory, V_axon read back)."""
+    size is measured over 2000 steps after `warmup` x 200 untimed ones (rt_search picks
+    the sizes).  Also: per-step latency with the host in the loop at that size (each
+    step's evoked input written from host memory, V_axon read back)."""
     from paper_1612_01501_gb300 import inputs
     rows = []
     for model, dens, p, n0 in RT_CASES:
-        tried, launches = {}, {}
+        launches = {}
 
-        def measure(N):
-            N = max(64, int(round(N / 64.0)) * 64)
-            if N in tried:
-                return N, tried[N]
+        def time_at(N):
             flags = ion.FLAG_KAHAN | (ion.FLAG_SGJ if model == "SGJ" else 0)
             kw = {}
             if model == "NGJ":
@@ -331,33 +368,10 @@ def rt_table(ion, torch, stream, warmup):
                 b.record()
                 torch.cuda.synchronize()
                 sim.sync()
-                tried[N] = a.elapsed_time(b) * 1e3 / 2000
                 launches[N] = sim.launches - l0
-            return N, tried[N]
+                return a.elapsed_time(b) * 1e3 / 2000
 
-        N, t = measure(n0)
-        for _ in range(4):   # model steps
-            a = max(t - 3.0, 0.05) / float(N) ** p
-            N, t = measure(((0.98 * RT_LIMIT_US - 3.0) / a) ** (1.0 / p))
-            ok = [k for k, v in tried.items() if v <= RT_LIMIT_US]
-            bad = [k for k, v in tried.items() if v > RT_LIMIT_US]
-            if ok and bad and min(bad) <= 1.02 * max(ok):
-                break
-        for _ in range(6):   # bisection
-            ok = [k for k, v in tried.items() if v <= RT_LIMIT_US]
-            bad = [k for k, v in tried.items() if v > RT_LIMIT_US]
-            if not ok:
-                measure(min(tried) // 2)
-                continue
-            if not bad:
-                measure(max(ok) * 1.1)
-                continue
-            lo, hi = max(ok), min(bad)
-            if hi <= 1.02 * lo or hi - lo <= 64:
-                break
-            measure((lo + hi) / 2)
-        ok = [k for k, v in tried.items() if v <= RT_LIMIT_US]
-        best = max(ok) if ok else None
+        best, tried = rt_search(time_at, n0, p)
         row = {"use_case": f"{model} ({int(round(dens * 100))} %)", "max_cells": best,
                "us_per_timestep": tried.get(best), "launches_timed": launches.get(best, 0),
                "measured_us_per_timestep": {str(k): round(v, 3) for k, v in sorted(tried.items())}}

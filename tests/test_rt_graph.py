@@ -6,6 +6,9 @@ graphs with a pair hash (bench.rt_graph): the pair {i, j} is a junction with pro
 `density`, decided once for both orders.  These checks hold for any correct draw: the CSR
 is well formed, symmetric, free of self loops, rows ascending, the realised density is
 within a few standard deviations of the asked one, and the draw is a function of the seed.
+
+The table's sizes come from a search over step times (bench.rt_search); on synthetic step
+time curves it must land within 2 % of the threshold a brute-force scan finds.
 """
 import os
 import sys
@@ -57,3 +60,49 @@ def test_rt_graph_depends_on_the_seed_only():
     c = bench.rt_graph(torch, 200, 0.3, seed=6, device="cpu")
     assert all(np.array_equal(x, y) for x, y in zip(a, b))
     assert not np.array_equal(a[1], c[1])
+
+
+# ---- the size search behind the real-time table --------------------------------------
+
+def _threshold(t_of_n, limit=50.0, q=64, hi=1 << 24):
+    """Largest multiple of q with t(N) <= limit, by brute force over multiples of q."""
+    best = None
+    n = q
+    while n <= hi and t_of_n(n) <= limit:
+        best = n
+        n += q
+    return best
+
+
+@pytest.mark.parametrize("p,n_star,n0", [(2, 18700, 16384), (2, 10400, 9216), (1, 1_200_000, 1 << 20),
+                                         (1, 2_290_000, 1 << 21), (2, 3000, 20000)])
+def test_rt_search_lands_within_two_percent_of_the_threshold(p, n_star, n0):
+    a = 47.0 / n_star ** p
+    t = lambda n: 3.0 + a * n ** p
+    best, tried = bench.rt_search(t, n0, p)
+    assert best is not None and t(best) <= 50.0
+    truth = _threshold(t, q=64, hi=4 * n_star)
+    assert truth * 0.98 <= best <= truth
+    assert all(n % 64 == 0 for n in tried) and len(tried) <= 11
+
+
+def test_rt_search_with_an_overhead_the_model_does_not_know():
+    """A fixed cost other than the model's 3 us and a little measurement noise: the bracket
+    still closes on the threshold."""
+    rng = np.random.default_rng(0)
+    t = lambda n: 9.0 + 41.0 * (n / 12000.0) ** 2 * (1.0 + 0.002 * rng.standard_normal())
+    best, tried = bench.rt_search(t, 6000, 2)
+    assert best is not None and tried[best] <= 50.0
+    assert 0.97 * 12000 <= best <= 12000 * 1.01
+    bigger = [n for n, v in tried.items() if n > best]
+    assert bigger and all(tried[n] > 50.0 for n in bigger)
+
+
+def test_rt_search_when_no_size_meets_the_limit():
+    best, tried = bench.rt_search(lambda n: 60.0 + n * 1e-6, 4096, 1)
+    assert best is None and min(tried) == 64
+
+
+def test_rt_search_when_every_size_meets_the_limit():
+    best, tried = bench.rt_search(lambda n: 10.0, 4096, 1)
+    assert best == max(tried) and best > 4096
