@@ -499,6 +499,27 @@ def test_sgj_csr_one_step(torch_cuda, O, n, k, weights, staging, index_bytes, st
     assert err.max() <= STEP_RTOL, err.max(axis=1)
 
 
+@pytest.mark.parametrize("kind", ["rgj", "sgj"])
+def test_staged_csr_with_rows_of_thousands_of_edges(torch_cuda, O, kind):
+    """A 4096-cell network with about 63 % of all pairs connected (rows of ~2600 edges, one
+    chunk): the staged kernel keeps the unpadded layout for such rows with the exponential
+    junction and the padded one with the linear junction; both reproduce the oracle's step."""
+    n = 4096
+    rp, col = inputs.random_symmetric_csr(n, n, 31)   # n/2 draws per cell: ~63 % of all pairs
+    assert len(col) / n > 1500
+    g = inputs.junction_weight(0.04, len(col) / n)
+    w = np.full(len(col), g, np.float32)
+    if kind == "sgj":
+        lay = {}
+        err = _sgj_one_step(O, n, O.CSR, rp=rp, col=col, w=w, tune=dict(csr_staging=2), layout=lay)
+    else:
+        lay = None
+        err = _one_step_case(O, "csr", n, O.CSR, rp=rp, col=col, w=w, warm=3, tune=dict(csr_staging=2))
+    assert err.max() <= STEP_RTOL, err.max(axis=1)
+    if lay is not None:
+        assert lay["staged"] == 1 and lay["index_bytes"] == 2
+
+
 def test_sgj_csr_trajectory_on_the_staged_kernel(torch_cuda, O):
     """Linear junctions through the staged compact kernel (two chunks) for 20 ms: within
     0.1 mV of the oracle."""
