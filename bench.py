@@ -80,6 +80,23 @@ TRAFFIC = {   # an entry is removed when its kernel changes, until it is capture
 }
 
 
+def traffic_for(key, kernel, variant, tune, dense_shape=""):
+    """(DRAM bytes per launch, summary) of the line's kernel from TRAFFIC, or None: only for
+    the graph-replayed variants (the surrogate line's included) and only when the launch
+    shape the line runs (the autotuner's table, or --dense-shape) matches every field the
+    capture fixes."""
+    tr = TRAFFIC.get((key, kernel))
+    if tr is None or variant not in ("graph", "exact", "surrogate"):
+        return None
+    shape = dict(tune or {})
+    if dense_shape:
+        R, W, GJ = (int(x) for x in dense_shape.split(","))
+        shape.update(dense_rows_per_warp=R, dense_warps=W, dense_col_splits=GJ)
+    if not all(shape.get(f) == v for f, v in tr[2].items()):
+        return None
+    return tr[0], tr[1]
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -848,13 +865,8 @@ def main():
             "gpu_launches": int(launches),
             "clocks": ck,
         }
-        tr = TRAFFIC.get((key, roof.get("kernel")))
-        shape = dict(variants[best]["tune"] or {})
-        if args.dense_shape:
-            R, W, GJ = (int(x) for x in args.dense_shape.split(","))
-            shape.update(dense_rows_per_warp=R, dense_warps=W, dense_col_splits=GJ)
-        if tr is not None and best in ("graph", "exact", "surrogate") and \
-                all(shape.get(f) == v for f, v in tr[2].items()):
+        tr = traffic_for(key, roof.get("kernel"), best, variants[best]["tune"], args.dense_shape)
+        if tr is not None:
             roof["traffic"] = tr[0]
             roof["traffic_source"] = tr[1] + " (one ncu capture of this kernel; the summary names its launch shape)"
         # the paper's real-time criterion: one time step (50 us of biological time) computed
